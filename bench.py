@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: spacetime DOF-updates/s of the MTP-SAT evolution on one GB300.
+
+Workload (default): 3D Maxwell, unit cube graded toward (0,0,0) with size ratio 8,
+32^3 x 6 = 196608 tets, p = 4 (q = 5 stages, m = 8 sub-intervals), eps = 4 in the
+ball of radius 0.25 around the centre, mu = 1, Gaussian E pulse (width 0.05, seeded
+centre), PEC walls, T = 0.5, tents pitched with causality factor 0.5.
+
+One step = one full evolve 0 -> T through every tent (all layers), state resident
+in HBM.  metric value = sum_i N_dof,i m q / step time (Sec. 5.2 of the paper).
+Also reported: the same metric end to end through the host-buffer C-ABI call, the
+plain FP64 GPU path on a truncated window of layers (same window for both modes),
+the roofline of the tent kernel, and the oracle on the host cores.
+
+--impl reference runs the FP64 CPU oracle (the only reference implementation of
+this method here) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+FP32_SM_LANES = 128            # FP32 FMA lanes per SM (Blackwell)
+N_SMS = 152
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def make_workload(name):
+    import mtp_synth as S
+    if name == "graded":
+        return S.graded_sphere(32, 4, 0.5)
+    if name == "cube":
+        return S.cube_mode(16, 3, 1.0)
+    if name == "small":
+        return S.graded_sphere(8, 4, 0.1)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def initial_lattice(w):
+    import mtp_synth as S
+    pts = S.lattice_points(w.verts, w.elems, w.p)
+    E, H = w.init(pts, 0.0)
+    fs = [0, 1, 5] if w.dim == 2 else [0, 1, 2, 3, 4, 5]
+    u = np.concatenate([E, H], -1)[..., fs]
+    mat = np.where(np.array(fs) < 3, 1.0, 0.0)
+    scale = mat[None, None, :] * w.eps[:, None, None] + (1 - mat[None, None, :]) * w.mu[:, None, None]
+    return np.ascontiguousarray(u * scale)
+
+
+def flops_per_dof_update(dim, p):
+    """Algorithmic minimum per DOF-update: volume d nf Np^2 + facets d nf 2 Nfp Np + mass solve and
+    M' 2 nf^2 Np multiply-adds per element and operator application, x2 flops, / (nf Np)."""
+    nf = 3 if dim == 2 else 6
+    nb = (p + 1) * (p + 2) // 2 if dim == 2 else (p + 1) * (p + 2) * (p + 3) // 6
+    nfb = p + 1 if dim == 2 else (p + 1) * (p + 2) // 2
+    mac = dim * nf * nb * nb + dim * nf * 2 * nfb * nb + 2 * nf * nf * nb
+    return 2.0 * mac / (nf * nb)
+
+
+def window_dofs(w, tents, lb, le, p, nrhs=1):
+    nf = 3 if w.dim == 2 else 6
+    nb = (p + 1) * (p + 2) // 2 if w.dim == 2 else (p + 1) * (p + 2) * (p + 3) // 6
+    psize = np.bincount(w.elems.ravel(), minlength=len(w.verts))
+    lp = tents["layer_ptr"]
+    v = tents["vertex"][lp[lb]:lp[le]]
+    return float(psize[v].sum()) * nf * nb * (2 * p) * (p + 1) * nrhs
+
+
+class Clocks:
+    """nvidia-smi sampler (every 200 ms) started before and stopped after the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+def cpu_baseline_sample(workload, n_tents, seed=7):
+    """Time the FP64 oracle (test infrastructure, as it stands) on a bounded sample of the
+    workload: the first n_tents tents of layer 0 from a seeded random state on the flat front.
+    Runs in a child process pinned to one BLAS thread; returns the JSON it prints."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", workload,
+                        "--cpu-tents", str(n_tents), "--seed", str(seed)],
+                       capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        return {"error": r.stderr[-400:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_worker(args):
+    from oracle.mesh import Mesh as OMesh
+    from oracle.mtp import Discretization
+    from oracle.pitch import pitch_first_round
+    w = make_workload(args.cpu_worker)
+    disc = Discretization(OMesh(w.verts, w.elems, w.eps, w.mu), w.p)
+    first = pitch_first_round(w.verts, w.elems, w.eps, w.mu, w.T, w.causality)
+    rng = np.random.default_rng(args.seed)
+    tau = np.zeros(len(w.verts))
+    done, dofs = 0, 0.0
+    t0 = time.perf_counter()
+    for V, tb, tt in first[: args.cpu_tents]:
+        patch = disc.mesh.patch[V]
+        Yp = rng.standard_normal((len(patch), disc.nf * disc.nb))
+        disc.sat_tent(V, tt - tb, tau, Yp)
+        done += 1
+        dofs += len(patch) * disc.nf * disc.nb * (2 * w.p) * (w.p + 1)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"value": dofs / dt, "seconds": dt, "tents": done, "dofs": dofs}))
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on host cores, bounded sample per step (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args.workload)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline_sample(args.workload, 2)
+    for s in range(args.steps):
+        vals.append(cpu_baseline_sample(args.workload, args.ref_tents, seed=100 + s))
+    rate = float(np.mean([v["value"] for v in vals]))
+    secs = float(np.mean([v["seconds"] for v in vals]))
+    line = {
+        "impl": "reference", "metric": "spacetime DOF-updates/s", "value": rate,
+        "unit": "DOF-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "elems": int(len(w.elems)), "p": w.p,
+                   "sample": f"{args.ref_tents} tents of layer 0 per step, seeded random state"},
+        "cpu_baseline": {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.ref_tents} tents of layer 0 per step"},
+        "e2e": {"value": rate, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_mtp(args):
+    import torch
+    import paper_1906_11029_gb300 as mtp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    peaks, peak_kind = load_peaks()
+    w = make_workload(args.workload)
+    prec = mtp.MTP_FP32 if args.precision == "fp32" else mtp.MTP_FP64
+    t0 = time.perf_counter()
+    mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=prec)
+    t1 = time.perf_counter()
+    tents = mesh.pitch(w.T, w.causality)
+    t2 = time.perf_counter()
+    tl = tents.get()
+    n_layers = tents.info["n_layers"]
+    launches_per_step = int(np.count_nonzero(np.diff(tl["layer_ptr"])))
+    dofs = tents.info["spacetime_dofs"]
+    vals0 = torch.tensor(initial_lattice(w)[None], device="cuda")
+    state0 = mesh.state_from_lattice(vals0)
+    del vals0
+    work = state0.clone()
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        work.copy_(state0)
+        tents.evolve(work)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for k in range(args.steps):
+        work.copy_(state0)
+        ev[k][0].record(stream)
+        tents.evolve(work)
+        ev[k][1].record(stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    total_ms = start.elapsed_time(end)
+    kern_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_max = torch.tensor([total_ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    total_ms = float(t_max.item())
+    value = world * args.steps * dofs / (total_ms / 1e3)
+
+    # roofline of the tent kernel (the evolve is the tent-kernel graph)
+    fl = flops_per_dof_update(w.dim, w.p)
+    launch_ms = kern_ms / (args.steps * launches_per_step)
+    flops_per_launch = dofs * fl / launches_per_step
+    if prec == mtp.MTP_FP32:
+        peak = N_SMS * FP32_SM_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        bound = "alu"
+    else:
+        peak = args.fp64_peak_tflops
+        bound = "alu"
+    achieved = flops_per_launch / (launch_ms / 1e3) / 1e12
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": f"tent_layer_kernel<{args.precision},3,{w.p}>",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)"}
+
+    # end to end through the host-buffer entry point (pinned buffers, copies in the timed region)
+    h_in = state0.cpu().pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    tents.evolve_host(h_in, h_out)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 2))
+    barrier()
+    te0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        tents.evolve_host(h_in, h_out)
+    te1 = time.perf_counter()
+    nbytes = h_in.numel() * h_in.element_size()
+    e2e = {"value": world * e2e_steps * dofs / (te1 - te0), "unit": "DOF-updates/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+           "call": "mtp_evolve_host (pinned host buffers)"}
+
+    # plain FP64 GPU path vs this path on the same truncated window of layers
+    fp64 = None
+    if args.fp64_window > 0 and prec != mtp.MTP_FP64:
+        lw = max(1, int(args.fp64_window * n_layers))
+        wd = window_dofs(w, tl, 0, lw, w.p)
+        mesh64 = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=mtp.MTP_FP64)
+        tents64 = mesh64.pitch(w.T, w.causality)
+        s64 = mesh64.state_from_lattice(torch.tensor(initial_lattice(w)[None], device="cuda"))
+        s64w = s64.clone()
+        tents64.evolve_layers(s64w, 0, 1)
+        torch.cuda.synchronize()
+        s64w.copy_(s64)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        tents64.evolve_layers(s64w, 0, lw)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b)
+        work.copy_(state0)
+        a.record(stream)
+        tents.evolve_layers(work, 0, lw)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms32 = a.elapsed_time(b)
+        u64 = mesh64.state_to_lattice(s64w).cpu().numpy()
+        u32 = mesh.state_to_lattice(work).cpu().numpy()
+        fp64 = {"window_layers": lw, "window_dof_updates": wd, "fp64_value": wd / (ms64 / 1e3),
+                "this_path_value_same_window": wd / (ms32 / 1e3), "speedup_vs_fp64": ms64 / ms32,
+                "rel_l2_vs_fp64_on_window": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64))}
+        del mesh64, tents64, s64, s64w
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        r = cpu_baseline_sample(args.workload, args.cpu_tents)
+        cpu = {"value": r.get("value"), "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {r.get('tents')} tents of layer 0 of the same workload, seeded random "
+                         f"state, FP64 numpy oracle, {r.get('seconds', 0):.1f} s", **({"error": r["error"]} if "error" in r else {})}
+
+    if rank == 0:
+        line = {
+            "metric": "spacetime DOF-updates/s", "value": value, "unit": "DOF-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == mtp.MTP_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": w.name, "elems": int(len(w.elems)), "p": w.p, "q": w.p + 1, "m": 2 * w.p,
+                       "T": w.T, "tents": tents.info["n_tents"], "layers": n_layers,
+                       "dof_updates_per_step": dofs, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "state larger than L2 (%.0f MB)" % (state0.numel() * state0.element_size() / 1e6),
+                       "pitch_s": t2 - t1, "mesh_s": t1 - t0},
+            "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "fp64_gpu": fp64,
+            "peaks": peak_kind,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mtp", choices=["mtp", "reference"])
+    ap.add_argument("--workload", default="graded", choices=["graded", "cube", "small"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fp64-window", type=float, default=0.02)
+    ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
+    ap.add_argument("--cpu-tents", type=int, default=12)
+    ap.add_argument("--ref-tents", type=int, default=6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-worker", default=None)
+    ap.add_argument("--seed", type=int, default=7)
+    args = ap.parse_args()
+    if args.cpu_worker:
+        return cpu_worker(args)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mtp(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,150 @@
+/*
+ * mtp.h — C ABI of the GB300 explicit Mapped Tent Pitching (MTP) library for the
+ * time-domain Maxwell equations with structure-aware Taylor (SAT) time stepping
+ * (Gopalakrishnan, Hochsteger, Schoeberl, Wintersteiger, arXiv:1906.11029).
+ *
+ * Problem (Sec. 3, eq. maxwell):  d_t(eps E) = curl H,  d_t(mu H) = -curl E  on a
+ * conforming simplicial mesh of a bounded domain (2D: TE fields Ex, Ey, Hz; 3D: E, H),
+ * eps and mu constant per element, perfectly conducting (PEC) boundary everywhere.
+ *
+ * Conventions for every call:
+ *   - Return value: MTP_OK (0) or a negative MTP_E* code; mtp_last_error() then gives
+ *     a thread-local message.  No C++ exception crosses this boundary.
+ *   - Host input arrays are read during the call and copied; the caller keeps ownership.
+ *   - Handles (mtp_mesh_t, mtp_tents_t) are owned by the library until *_destroy.
+ *     A tents handle refers to its mesh: destroy tents before the mesh.
+ *   - "dev" pointers are CUDA device pointers owned by the caller (e.g. PyTorch
+ *     tensors); "stream" is a cudaStream_t passed as void* (NULL = legacy default).
+ *     Device work is enqueued on that stream; calls return when it is enqueued
+ *     unless stated otherwise.
+ *   - State layout ("library layout"): state[r][e][f][a], r < n_rhs, e < n_elems,
+ *     f < n_fields, a < n_basis, in the mesh's precision (double for MTP_FP64, float
+ *     for MTP_FP32).  The coefficients are those of the conserved variable
+ *     y = g(u) - f(u) grad(phi) (Sec. 3, transformed equation; y = (eps E, mu H) on
+ *     a flat front) in an L2-orthonormal basis of P_p on each element.
+ *   - Lattice layout: vals[r][e][k][f] in double, the value of y at lattice point k
+ *     of element e.  Lattice points: with s_0 < ... < s_d the element's vertex ids
+ *     sorted ascending, point k is v_{s0} + sum_l (i_l/p)(v_{sl} - v_{s0}) for the
+ *     k-th integer tuple (i_1..i_d), sum <= p, enumerated with i_d outermost and i_1
+ *     innermost.  P_p is unisolvent on this lattice, so it exchanges states with any
+ *     other discretisation of the same space without sharing a basis.
+ */
+#ifndef MTP_H
+#define MTP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define MTP_OK            0
+#define MTP_EINVAL       -1   /* bad argument (null pointer, size, option, T mismatch) */
+#define MTP_EMESH        -2   /* degenerate or non-conforming mesh */
+#define MTP_ECAUSAL      -3   /* a tent violates |grad phi| < sqrt(eps mu) or t_top <= t_bot */
+#define MTP_ENOMEM       -4   /* host or device allocation failed */
+#define MTP_ECUDA        -5   /* a CUDA runtime call failed (message has the CUDA error) */
+#define MTP_ETIMEOUT     -6   /* a bounded device-side wait expired */
+#define MTP_ENUMERIC     -7   /* NaN / Inf detected */
+#define MTP_EUNSUPPORTED -8   /* combination not built (e.g. degree > 4, patch too large) */
+
+/* precision of the state and of the operator arithmetic */
+#define MTP_FP64 0
+#define MTP_FP32 1
+
+typedef struct mtp_mesh*  mtp_mesh_t;
+typedef struct mtp_tents* mtp_tents_t;
+
+typedef struct {
+    int p;          /* polynomial degree of V_h, 1..4 (Sec. 3, DG space)                   */
+    int q;          /* SAT stages; 0 selects p+1 (Sec. 5.1)                                */
+    int m;          /* SAT sub-intervals per tent; 0 selects 2p (Sec. 5.1)                 */
+    int precision;  /* MTP_FP64 or MTP_FP32                                                */
+    int n_rhs;      /* independent states evolved with the same tents (>= 1; 0 means 1)   */
+    int flags;      /* reserved, must be 0                                                 */
+} mtp_options;
+
+/* Spatial mesh and materials (Sec. 2: conforming mesh of elements T and vertices V;
+ * Sec. 3: eps, mu per element).  vertices[n_verts][dim], elements[n_elems][dim+1]
+ * (0-based vertex ids, any orientation), eps/mu[n_elems] > 0.  Host only: validates
+ * (MTP_EMESH on zero-volume elements, repeated vertices or a facet shared by more
+ * than two elements), builds facets, neighbours, vertex patches, FP64 element
+ * geometry and the reference tables of degree p.  No device memory is touched here. */
+int mtp_mesh_create(int dim, int64_t n_verts, const double* vertices,
+                    int64_t n_elems, const int32_t* elements,
+                    const double* eps, const double* mu,
+                    const mtp_options* opts, mtp_mesh_t* out);
+void mtp_mesh_destroy(mtp_mesh_t mesh);
+
+/* Sizes: n_fields = 3 (2D TE) or 6 (3D); n_basis = dim P_p; max_patch = largest
+ * vertex patch |omega_V|.  Any output pointer may be NULL. */
+int mtp_mesh_info(mtp_mesh_t mesh, int* dim, int* n_fields, int* n_basis,
+                  int64_t* n_elems, int64_t* n_verts, int* max_patch);
+
+/* Tent pitching to time T (Sec. 2).  Host only, deterministic FP64 (timed separately
+ * from evolution).  wavespeed[n_elems] (NULL: 1/sqrt(eps mu)); causality_factor in
+ * (0, 1): every front satisfies |grad tau| <= causality_factor / c on every element
+ * (0.5 reproduces the slope bound 1/(2c) of Sec. 5.1).  Rule: per vertex
+ * k_V = min element height at V; edge bound b_VW = cf min(k_V, k_W) / (d c_VW) with
+ * c_VW the largest wave speed on the edge; rounds move every strict local minimum of
+ * (tau, vertex id) to min(T, min_W tau_W + b_VW); tent layer = 1 + max(layer of the
+ * previous tents at V and its neighbours).  Tents of one layer have disjoint patches
+ * (Sec. 2: vertices at graph distance >= 2 are independent).  Output sorted by
+ * (layer, vertex). */
+int mtp_pitch_tents(mtp_mesh_t mesh, const double* wavespeed, double causality_factor,
+                    double T, mtp_tents_t* out);
+void mtp_tents_destroy(mtp_tents_t tents);
+
+/* n_tents, n_layers, and the spacetime DOF count of one evolve (Sec. 5.2):
+ * sum_i N_dof,i * m * q * n_rhs with N_dof,i = n_fields * n_basis * |omega_V|.
+ * Any output pointer may be NULL. */
+int mtp_tents_info(mtp_tents_t tents, int64_t* n_tents, int64_t* n_layers,
+                   double* spacetime_dofs);
+
+/* Copy the tent list to host arrays vertex/t_bot/t_top/layer[n_tents] and
+ * layer_ptr[n_layers+1] (tents of layer l are [layer_ptr[l], layer_ptr[l+1])).
+ * Any pointer may be NULL. */
+int mtp_tents_get(mtp_tents_t tents, int32_t* vertex, double* t_bot, double* t_top,
+                  int32_t* layer, int64_t* layer_ptr);
+
+/* Lattice values of y (FP64, lattice layout, dev) -> state (library layout, dev).
+ * Exact up to rounding for y in P_p on each element. */
+int mtp_state_from_lattice(mtp_mesh_t mesh, const double* vals_dev, void* state_dev,
+                           void* stream);
+/* State (dev) -> lattice values of y (FP64, dev). */
+int mtp_state_to_lattice(mtp_mesh_t mesh, const void* state_dev, double* vals_dev,
+                         void* stream);
+
+/* Evolve the state in place from the flat front t = 0 to the flat front t = T through
+ * every tent, layer by layer (Sec. 2 and 3), each tent advanced bottom to top with
+ * q-stage SAT over m sub-intervals (Sec. 4, eqs. coeff_rec and recursion-init), with
+ * the mass solve in the closed form of Sec. 4.  All tents of a layer (times n_rhs)
+ * run in one kernel launch; the layers are replayed from a CUDA graph.  T must equal
+ * the pitched T (MTP_EINVAL otherwise).  Asynchronous on the stream. */
+int mtp_evolve(mtp_tents_t tents, void* state_dev, double T, void* stream);
+
+/* Apply only layers [layer_begin, layer_end) to a state that sits on the front just
+ * before layer_begin (each vertex at the top of its last earlier tent). */
+int mtp_evolve_layers(mtp_tents_t tents, void* state_dev, int64_t layer_begin,
+                      int64_t layer_end, void* stream);
+
+/* mtp_evolve on host buffers: copies state_in_host (library layout) to a device buffer
+ * owned by the tents handle, evolves, copies the result to state_out_host, and
+ * synchronises the stream before returning.  state_in_host may equal state_out_host. */
+int mtp_evolve_host(mtp_tents_t tents, const void* state_in_host, void* state_out_host,
+                    double T, void* stream);
+
+/* Electromagnetic energy of a state on a flat front, per right-hand side:
+ * out_host[r] = 1/2 sum_T int_T (|y_E|^2 / eps + |y_H|^2 / mu)  (= 1/2 int eps|E|^2 + mu|H|^2).
+ * Synchronises the stream. */
+int mtp_energy(mtp_mesh_t mesh, const void* state_dev, double* out_host, void* stream);
+
+/* Thread-local description of the last error returned on this thread. */
+const char* mtp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MTP_H */

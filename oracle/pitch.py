@@ -67,8 +67,9 @@ def element_heights(verts, elems):
     return H, s
 
 
-def pitch_tents(verts, elems, eps, mu, T, cf=0.5, wavespeed=None):
-    """Returns dict(vertex, t_bot, t_top, layer, layer_ptr) sorted by (layer, vertex)."""
+def pitch_tents(verts, elems, eps, mu, T, cf=0.5, wavespeed=None, max_rounds=None):
+    """Returns dict(vertex, t_bot, t_top, layer, layer_ptr) sorted by (layer, vertex).
+    ``max_rounds`` stops after that many rounds (the front is then not at T)."""
     verts = np.asarray(verts, float)
     nv, d = verts.shape
     H, s = element_heights(verts, elems)
@@ -107,7 +108,9 @@ def pitch_tents(verts, elems, eps, mu, T, cf=0.5, wavespeed=None):
     tau = np.zeros(nv)
     last = np.full(nv, -1, np.int64)
     tv, tb, tt, tl = [], [], [], []
-    while True:
+    rounds = 0
+    while max_rounds is None or rounds < max_rounds:
+        rounds += 1
         active = tau < T
         if not active.any():
             break
@@ -137,3 +140,9 @@ def pitch_tents(verts, elems, eps, mu, T, cf=0.5, wavespeed=None):
     layer_ptr = np.cumsum(layer_ptr)
     return {"vertex": v.astype(np.int32), "t_bot": b, "t_top": t, "layer": lay.astype(np.int32),
             "layer_ptr": layer_ptr, "k": k}
+
+
+def pitch_first_round(verts, elems, eps, mu, T, cf=0.5, wavespeed=None):
+    """Tents of the first round (all in layer 0, from the flat front t = 0): [(V, t_bot, t_top)]."""
+    r = pitch_tents(verts, elems, eps, mu, T, cf, wavespeed, max_rounds=1)
+    return [(int(v), float(b), float(t)) for v, b, t in zip(r["vertex"], r["t_bot"], r["t_top"])]

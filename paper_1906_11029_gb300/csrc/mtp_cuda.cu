@@ -1,0 +1,392 @@
+// Device-side management of the MTP library: uploads, lattice exchange, energy,
+// and the layer-by-layer evolution driver (layers replayed from a CUDA graph).
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "mtp_internal.h"
+#include "mtp_launch.cuh"
+
+namespace mtp {
+
+#define CUDA_TRY(call)                                                                       \
+    do {                                                                                     \
+        cudaError_t _e = (call);                                                             \
+        if (_e != cudaSuccess)                                                               \
+            return set_error(_e == cudaErrorMemoryAllocation ? MTP_ENOMEM : MTP_ECUDA,       \
+                             std::string(#call) + ": " + cudaGetErrorString(_e));            \
+    } while (0)
+
+struct DeviceMesh {
+    int device = -1;
+    double* geo = nullptr;
+    int32_t* elems = nullptr;
+    int64_t* patch_ptr = nullptr;
+    int32_t* patch_elem = nullptr;
+    int8_t* patch_info = nullptr;
+    void* S = nullptr;
+    void* Tr = nullptr;
+    void* L = nullptr;
+    double* V = nullptr;
+    double* Vinv = nullptr;
+    double* partial = nullptr;    // energy reduction scratch: [n_rhs][kEnergyBlocks] partials, then [n_rhs] sums
+};
+
+struct DeviceTents {
+    int32_t* v = nullptr;
+    double* tb = nullptr;
+    double* tt = nullptr;
+    double* tau = nullptr;
+    int* err = nullptr;
+    int* err_host = nullptr;      // pinned
+    void* host_state = nullptr;   // device buffer for mtp_evolve_host
+    cudaStream_t capture = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void* graph_state = nullptr;  // state pointer baked into the graph
+};
+
+constexpr int kEnergyBlocks = 304;
+constexpr int kEnergyThreads = 256;
+
+static size_t real_size(const Mesh& m) { return m.precision == MTP_FP64 ? sizeof(double) : sizeof(float); }
+
+template <typename T>
+static int upload(T** dst, const T* src, size_t n) {
+    CUDA_TRY(cudaMalloc((void**)dst, n * sizeof(T) + 16));
+    CUDA_TRY(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return MTP_OK;
+}
+
+static int upload_real(const Mesh& m, void** dst, const std::vector<double>& src) {
+    if (m.precision == MTP_FP64) return upload((double**)dst, src.data(), src.size());
+    std::vector<float> f(src.begin(), src.end());
+    return upload((float**)dst, f.data(), f.size());
+}
+
+#define MTP_TRY(call)                  \
+    do {                               \
+        int _rc = (call);              \
+        if (_rc != MTP_OK) return _rc; \
+    } while (0)
+
+int device_mesh_upload(Mesh& m) {
+    int dev;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (m.dev) {
+        if (m.dev->device == dev) return MTP_OK;
+        return set_error(MTP_EINVAL, "mesh was uploaded to another device");
+    }
+    m.dev = new DeviceMesh();
+    DeviceMesh& d = *m.dev;
+    d.device = dev;
+    MTP_TRY(upload(&d.geo, m.geo.data(), m.geo.size()));
+    MTP_TRY(upload(&d.elems, m.elems.data(), m.elems.size()));
+    MTP_TRY(upload(&d.patch_ptr, m.patch_ptr.data(), m.patch_ptr.size()));
+    MTP_TRY(upload(&d.patch_elem, m.patch_elem.data(), m.patch_elem.size()));
+    MTP_TRY(upload(&d.patch_info, m.patch_info.data(), m.patch_info.size()));
+    MTP_TRY(upload_real(m, &d.S, m.ref.S));
+    MTP_TRY(upload_real(m, &d.Tr, m.ref.Tr));
+    MTP_TRY(upload_real(m, &d.L, m.ref.L));
+    MTP_TRY(upload(&d.V, m.ref.V.data(), m.ref.V.size()));
+    MTP_TRY(upload(&d.Vinv, m.ref.Vinv.data(), m.ref.Vinv.size()));
+    CUDA_TRY(cudaMalloc((void**)&d.partial, sizeof(double) * (kEnergyBlocks + 1) * m.n_rhs));
+    return MTP_OK;
+}
+
+void device_mesh_free(Mesh& m) {
+    if (!m.dev) return;
+    DeviceMesh& d = *m.dev;
+    void* ptrs[] = {d.geo, d.elems, d.patch_ptr, d.patch_elem, d.patch_info, d.S, d.Tr, d.L, d.V, d.Vinv, d.partial};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete m.dev;
+    m.dev = nullptr;
+}
+
+void device_tents_free(Tents& t) {
+    if (!t.dev) return;
+    DeviceTents& d = *t.dev;
+    if (d.exec) cudaGraphExecDestroy(d.exec);
+    if (d.capture) cudaStreamDestroy(d.capture);
+    void* ptrs[] = {d.v, d.tb, d.tt, d.tau, d.err, d.host_state};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (d.err_host) cudaFreeHost(d.err_host);
+    delete t.dev;
+    t.dev = nullptr;
+}
+
+static int device_tents_upload(Tents& t) {
+    MTP_TRY(device_mesh_upload(*t.mesh));
+    if (t.dev) return MTP_OK;
+    t.dev = new DeviceTents();
+    DeviceTents& d = *t.dev;
+    MTP_TRY(upload(&d.v, t.vertex.data(), t.vertex.size()));
+    MTP_TRY(upload(&d.tb, t.t_bot.data(), t.t_bot.size()));
+    MTP_TRY(upload(&d.tt, t.t_top.data(), t.t_top.size()));
+    CUDA_TRY(cudaMalloc((void**)&d.tau, sizeof(double) * t.mesh->nv));
+    CUDA_TRY(cudaMalloc((void**)&d.err, sizeof(int)));
+    CUDA_TRY(cudaMallocHost((void**)&d.err_host, sizeof(int)));
+    CUDA_TRY(cudaStreamCreateWithFlags(&d.capture, cudaStreamNonBlocking));
+    return MTP_OK;
+}
+
+static const KernelEntry& kernel_entry(const Mesh& m) {
+    static KernelEntry f64[2][4], f32[2][4];
+    static bool init = false;
+    if (!init) {
+        kernel_table_f64(f64);
+        kernel_table_f32(f32);
+        init = true;
+    }
+    return (m.precision == MTP_FP64 ? f64 : f32)[m.dim - 2][m.p - 1];
+}
+
+// ---------------------------------------------------------------------------------
+// lattice exchange: y(x_k) = (1/sqrt|det J|) sum_a V[k][a] Y_a and its inverse
+// ---------------------------------------------------------------------------------
+template <typename Real>
+__global__ void from_lattice_kernel(const double* vals, Real* state, const double* geo, const double* Vinv,
+                                    int64_t ne, int nf, int nb, int nrhs) {
+    const int64_t n = (int64_t)nrhs * ne * nb;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t re = i / nb;
+        const int a = (int)(i - re * nb);
+        const int64_t e = re % ne;
+        const double sq = 1.0 / geo[e * kGeoStride + 28];
+        const double* v = vals + re * nb * nf;
+        for (int f = 0; f < nf; ++f) {
+            double acc = 0;
+            for (int k = 0; k < nb; ++k) acc += Vinv[a * nb + k] * v[k * nf + f];
+            state[(re * nf + f) * nb + a] = (Real)(sq * acc);
+        }
+    }
+}
+
+template <typename Real>
+__global__ void to_lattice_kernel(const Real* state, double* vals, const double* geo, const double* V,
+                                  int64_t ne, int nf, int nb, int nrhs) {
+    const int64_t n = (int64_t)nrhs * ne * nb;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t re = i / nb;
+        const int k = (int)(i - re * nb);
+        const int64_t e = re % ne;
+        const double is = geo[e * kGeoStride + 28];
+        for (int f = 0; f < nf; ++f) {
+            double acc = 0;
+            for (int a = 0; a < nb; ++a) acc += V[k * nb + a] * (double)state[(re * nf + f) * nb + a];
+            vals[(re * nb + k) * nf + f] = is * acc;
+        }
+    }
+}
+
+static int grid_for(int64_t n, int threads) {
+    int64_t g = (n + threads - 1) / threads;
+    if (g > 152 * 64) g = 152 * 64;
+    return (int)(g < 1 ? 1 : g);
+}
+
+int device_from_lattice(Mesh& m, const double* vals, void* state, void* stream) {
+    MTP_TRY(device_mesh_upload(m));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = (int64_t)m.n_rhs * m.ne * m.nb;
+    if (m.precision == MTP_FP64)
+        from_lattice_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(vals, (double*)state, m.dev->geo, m.dev->Vinv,
+                                                                       m.ne, m.nf, m.nb, m.n_rhs);
+    else
+        from_lattice_kernel<float><<<grid_for(n, 256), 256, 0, st>>>(vals, (float*)state, m.dev->geo, m.dev->Vinv,
+                                                                      m.ne, m.nf, m.nb, m.n_rhs);
+    CUDA_TRY(cudaGetLastError());
+    return MTP_OK;
+}
+
+int device_to_lattice(Mesh& m, const void* state, double* vals, void* stream) {
+    MTP_TRY(device_mesh_upload(m));
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = (int64_t)m.n_rhs * m.ne * m.nb;
+    if (m.precision == MTP_FP64)
+        to_lattice_kernel<double><<<grid_for(n, 256), 256, 0, st>>>((const double*)state, vals, m.dev->geo, m.dev->V,
+                                                                     m.ne, m.nf, m.nb, m.n_rhs);
+    else
+        to_lattice_kernel<float><<<grid_for(n, 256), 256, 0, st>>>((const float*)state, vals, m.dev->geo, m.dev->V,
+                                                                    m.ne, m.nf, m.nb, m.n_rhs);
+    CUDA_TRY(cudaGetLastError());
+    return MTP_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// energy on a flat front: 1/2 sum (|Y_E|^2/eps + |Y_H|^2/mu); two-pass deterministic
+// reduction through the per-block partials buffer
+// ---------------------------------------------------------------------------------
+template <typename Real>
+__global__ void energy_partial_kernel(const Real* state, const double* geo, int64_t ne, int nf, int nb,
+                                      double* partial) {
+    __shared__ double red[kEnergyThreads];
+    const int rhs = blockIdx.y;
+    const Real* s = state + (int64_t)rhs * ne * nf * nb;
+    const int64_t n = ne * nf * nb;
+    double acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = i / (nf * nb);
+        const int f = (int)((i / nb) % nf);
+        const double y = (double)s[i];
+        const double* g = geo + e * kGeoStride;
+        const bool isE = nf == 6 ? f < 3 : f < 2;   // E fields first, then H (2D: Ex, Ey | Hz)
+        acc += y * y / (isE ? g[29] : g[30]);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[rhs * gridDim.x + blockIdx.x] = red[0];
+}
+
+__global__ void energy_final_kernel(const double* partial, int nblocks, double* out) {
+    __shared__ double red[kEnergyThreads];
+    const int rhs = blockIdx.x;
+    double acc = 0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += partial[rhs * nblocks + i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[rhs] = 0.5 * red[0];
+}
+
+int device_energy(Mesh& m, const void* state, double* out_host, void* stream) {
+    MTP_TRY(device_mesh_upload(m));
+    cudaStream_t st = (cudaStream_t)stream;
+    dim3 grid(kEnergyBlocks, m.n_rhs);
+    if (m.precision == MTP_FP64)
+        energy_partial_kernel<double><<<grid, kEnergyThreads, 0, st>>>((const double*)state, m.dev->geo, m.ne, m.nf,
+                                                                        m.nb, m.dev->partial);
+    else
+        energy_partial_kernel<float><<<grid, kEnergyThreads, 0, st>>>((const float*)state, m.dev->geo, m.ne, m.nf,
+                                                                       m.nb, m.dev->partial);
+    CUDA_TRY(cudaGetLastError());
+    double* out_dev = m.dev->partial + (size_t)kEnergyBlocks * m.n_rhs;
+    energy_final_kernel<<<m.n_rhs, kEnergyThreads, 0, st>>>(m.dev->partial, kEnergyBlocks, out_dev);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(out_host, out_dev, sizeof(double) * m.n_rhs, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return MTP_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// evolution
+// ---------------------------------------------------------------------------------
+static void fill_args(Tents& t, void* state, KArgs& a) {
+    Mesh& m = *t.mesh;
+    DeviceMesh& dm = *m.dev;
+    DeviceTents& dt = *t.dev;
+    std::memset(&a, 0, sizeof(a));
+    a.tent_v = dt.v;
+    a.tent_tb = dt.tb;
+    a.tent_tt = dt.tt;
+    a.patch_ptr = dm.patch_ptr;
+    a.patch_elem = dm.patch_elem;
+    a.patch_info = dm.patch_info;
+    a.elems = dm.elems;
+    a.geo = dm.geo;
+    a.tau = dt.tau;
+    a.S = dm.S;
+    a.Tr = dm.Tr;
+    a.L = dm.L;
+    a.state = state;
+    a.rhs_stride = m.ne * m.nf * m.nb;
+    a.err = dt.err;
+    a.q = m.q;
+    a.m = m.m;
+    a.max_patch = m.max_patch;
+    double f = 1.0;
+    for (int n = 0; n < kMaxTaylor; ++n) {
+        if (n > 0) f = f / (double)m.m / (double)n;
+        a.taylor[n] = f;
+    }
+}
+
+static int enqueue_layers(Tents& t, const KArgs& a, int64_t lb, int64_t le, cudaStream_t st) {
+    const KernelEntry& ke = kernel_entry(*t.mesh);
+    for (int64_t l = lb; l < le; ++l) {
+        const int64_t t0 = t.layer_ptr[l];
+        const int64_t n = t.layer_ptr[l + 1] - t0;
+        if (n == 0) continue;
+        CUDA_TRY(ke.launch(a, t0, (int)n, t.mesh->n_rhs, st));
+    }
+    return MTP_OK;
+}
+
+static int check_error_word(Tents& t, cudaStream_t st) {
+    DeviceTents& d = *t.dev;
+    CUDA_TRY(cudaMemcpyAsync(d.err_host, d.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (*d.err_host == 1) return set_error(MTP_ECAUSAL, "a tent violated |grad phi| < sqrt(eps mu)");
+    if (*d.err_host == 2) return set_error(MTP_ENUMERIC, "non-finite value in the evolved state");
+    if (*d.err_host != 0) return set_error(MTP_ECUDA, "unknown device error word");
+    return MTP_OK;
+}
+
+int device_evolve(Tents& t, void* state, int64_t lb, int64_t le, bool use_graph, void* stream) {
+    MTP_TRY(device_tents_upload(t));
+    Mesh& m = *t.mesh;
+    DeviceTents& d = *t.dev;
+    cudaStream_t st = (cudaStream_t)stream;
+    const KernelEntry& ke = kernel_entry(m);
+    size_t smem = 0;
+    CUDA_TRY(ke.prepare(m.max_patch, &smem));
+    int dev, smem_max;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if ((int64_t)smem > smem_max)
+        return set_error(MTP_EUNSUPPORTED, "tent kernel needs " + std::to_string(smem) +
+                                               " bytes of shared memory per block; the device allows " +
+                                               std::to_string(smem_max));
+    // front before layer lb
+    std::vector<double> tau(m.nv, 0.0);
+    for (int64_t i = 0; i < t.layer_ptr[lb]; ++i) tau[t.vertex[i]] = std::fmax(tau[t.vertex[i]], t.t_top[i]);
+    CUDA_TRY(cudaMemcpyAsync(d.tau, tau.data(), sizeof(double) * m.nv, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(d.err, 0, sizeof(int), st));
+    KArgs a;
+    fill_args(t, state, a);
+    if (use_graph && lb == 0 && le == (int64_t)t.layer_ptr.size() - 1) {
+        if (!d.exec || d.graph_state != state) {
+            if (d.exec) { cudaGraphExecDestroy(d.exec); d.exec = nullptr; }
+            cudaGraph_t g;
+            CUDA_TRY(cudaStreamBeginCapture(d.capture, cudaStreamCaptureModeThreadLocal));
+            int rc = enqueue_layers(t, a, lb, le, d.capture);
+            cudaError_t ce = cudaStreamEndCapture(d.capture, &g);
+            if (rc != MTP_OK) return rc;
+            CUDA_TRY(ce);
+            CUDA_TRY(cudaGraphInstantiate(&d.exec, g, 0));
+            cudaGraphDestroy(g);
+            d.graph_state = state;
+        }
+        CUDA_TRY(cudaGraphLaunch(d.exec, st));
+    } else {
+        MTP_TRY(enqueue_layers(t, a, lb, le, st));
+    }
+    return check_error_word(t, st);
+}
+
+int device_evolve_host(Tents& t, const void* in, void* out, void* stream) {
+    MTP_TRY(device_tents_upload(t));
+    Mesh& m = *t.mesh;
+    DeviceTents& d = *t.dev;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)m.n_rhs * m.ne * m.nf * m.nb * real_size(m);
+    if (!d.host_state) CUDA_TRY(cudaMalloc(&d.host_state, bytes));
+    CUDA_TRY(cudaMemcpyAsync(d.host_state, in, bytes, cudaMemcpyHostToDevice, st));
+    MTP_TRY(device_evolve(t, d.host_state, 0, (int64_t)t.layer_ptr.size() - 1, true, stream));
+    CUDA_TRY(cudaMemcpyAsync(out, d.host_state, bytes, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return MTP_OK;
+}
+
+}  // namespace mtp

@@ -1,0 +1,440 @@
+// CUDA kernels of the MTP-SAT hot path (sm_103a).
+//
+// One CTA evolves one tent (for one right-hand side) from bottom to top:
+//   (a) gather  the patch's state Y (all elements of omega_V) and FP64 geometry
+//   (b) operator A U: facet traces -> upwind / PEC flux -> lambda_V-weighted volume
+//       term + lift (Sec. 3, mapped DG semi-discretisation)
+//   (c) SAT recursion (Sec. 4, eqs. coeff_rec / recursion-init) with the closed-form
+//       pointwise mass inverse of Sec. 4, all m*q stages on shared-memory data
+//   (d) scatter the tent-top Y (patches of one layer are element-disjoint: no atomics)
+//
+// Discretisation on each element T of the patch (orthonormal basis psi_a, mass = I):
+//   volume:  Y_E[a] += -sum_l a_l x P_{l,H}[a],   Y_H[a] += sum_l a_l x P_{l,E}[a]
+//            with a_l = dt grad(lambda_{l+1}) and P_{l,s}[a] = sum_b S[j][l][a][b] U_s[b],
+//            S[j][l][a][b] = int lambda_j psi_b d_l psi_a on the reference simplex
+//            (delta = dt lambda_V with V the local vertex j of T).
+//   facets containing V: trace coefficients tr = Tr_f U / sqrt|det J| in the facet's
+//            orthonormal basis (facet parametrised on the ascending vertex ids, so the two
+//            sides agree), flux F*(tr-, tr+) pointwise on coefficients (the flux is linear
+//            with constant coefficients on a flat facet), lift
+//            Y[a] -= dt (d-1)!|F| / sqrt|det J| sum_c L[j][f][a][c] F*[c].
+//   mass:    U = G(t_i)^-1 Y per coefficient (6x6, closed form of Sec. 4, built in FP64)
+//            M' U = [-H x dt grad(lambda_j) ; E x dt grad(lambda_j)].
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mtp {
+
+constexpr int kMaxTaylor = 9;
+
+struct KArgs {
+    const int32_t* tent_v;
+    const double* tent_tb;
+    const double* tent_tt;
+    const int64_t* patch_ptr;
+    const int32_t* patch_elem;
+    const int8_t* patch_info;   // [entry][12]: j, slot[4], nbr_face[4] (see mtp_internal.h)
+    const int32_t* elems;       // [ne][dim+1] sorted vertex ids
+    const double* geo;          // [ne][32]
+    double* tau;                // vertex times of the current front
+    const void* S;              // reference tables in the state precision
+    const void* Tr;
+    const void* L;
+    void* state;                // [rhs][ne][nf][nb]
+    int64_t rhs_stride;         // ne * nf * nb
+    int* err;                   // error word (0 = ok, 1 = causality, 2 = non-finite)
+    int q, m;
+    int max_patch;
+    double taylor[kMaxTaylor];  // (1/m)^n / n!
+};
+
+template <int DIM, int P>
+struct Shape {
+    static constexpr int NF = DIM == 2 ? 3 : 6;
+    static constexpr int NB = DIM == 2 ? (P + 1) * (P + 2) / 2 : (P + 1) * (P + 2) * (P + 3) / 6;
+    static constexpr int NFB = DIM == 2 ? P + 1 : (P + 1) * (P + 2) / 2;
+    static constexpr int NV = DIM + 1;
+    static constexpr int NT = DIM == 2 ? 128 : 256;   // threads per CTA
+};
+
+// shared-memory carve-up, sizes from the mesh's largest patch
+template <typename Real, int DIM, int P>
+struct SmemLayout {
+    using Sh = Shape<DIM, P>;
+    static __host__ __device__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+    size_t off_Y, off_Ua, off_Ub, off_tr, off_Gi, off_gphi, off_gdel, off_mat, off_ac, off_gd, off_nrm,
+        off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, bytes;
+    __host__ __device__ explicit SmemLayout(int mp) {
+        size_t o = 0;
+        const size_t state = (size_t)mp * Sh::NF * Sh::NB * sizeof(Real);
+        off_Y = o; o = align16(o + state);
+        off_Ua = o; o = align16(o + state);
+        off_Ub = o; o = align16(o + state);
+        off_tr = o; o = align16(o + (size_t)mp * DIM * Sh::NF * Sh::NFB * sizeof(Real));
+        off_Gi = o; o = align16(o + (size_t)mp * Sh::NF * Sh::NF * sizeof(Real));
+        off_gphi = o; o = align16(o + (size_t)mp * 3 * sizeof(double));
+        off_gdel = o; o = align16(o + (size_t)mp * 3 * sizeof(double));
+        off_mat = o; o = align16(o + (size_t)mp * 2 * sizeof(double));
+        off_ac = o; o = align16(o + (size_t)mp * DIM * 3 * sizeof(Real));
+        off_gd = o; o = align16(o + (size_t)mp * 3 * sizeof(Real));
+        off_nrm = o; o = align16(o + (size_t)mp * DIM * 3 * sizeof(Real));
+        off_liftc = o; o = align16(o + (size_t)mp * DIM * sizeof(Real));
+        off_trs = o; o = align16(o + (size_t)mp * sizeof(Real));
+        off_Z = o; o = align16(o + (size_t)mp * (1 + DIM) * sizeof(Real));
+        off_j = o; o = align16(o + (size_t)mp);
+        off_nslot = o; o = align16(o + (size_t)mp * DIM);
+        off_nfi = o; o = align16(o + (size_t)mp * DIM);
+        bytes = o;
+    }
+};
+
+// Upwind flux on coefficient vectors (Sec. 3 upwind flux, impedance form; PEC = mirror
+// state E+ = -E-, H+ = H-).  um/up/out in the 6-component (E, H) ordering.
+template <typename Real>
+__device__ __forceinline__ void upwind6(const Real um[6], const Real up[6], const Real n[3], Real Zm, Real Zp,
+                                        Real out[6]) {
+    Real Emn = um[0] * n[0] + um[1] * n[1] + um[2] * n[2];
+    Real Epn = up[0] * n[0] + up[1] * n[1] + up[2] * n[2];
+    Real Emt[3], Ept[3], dH[3];
+    for (int c = 0; c < 3; ++c) {
+        Emt[c] = um[c] - Emn * n[c];
+        Ept[c] = up[c] - Epn * n[c];
+        dH[c] = um[3 + c] - up[3 + c];
+    }
+    const Real inv = Real(1) / (Zm + Zp);
+    // H* x n = (Zm Hm x n + Zp Hp x n + Emt - Ept) / (Zm + Zp)
+    Real hx[3] = {Zm * um[3] + Zp * up[3], Zm * um[4] + Zp * up[4], Zm * um[5] + Zp * up[5]};
+    out[0] = (hx[1] * n[2] - hx[2] * n[1] + Emt[0] - Ept[0]) * inv;
+    out[1] = (hx[2] * n[0] - hx[0] * n[2] + Emt[1] - Ept[1]) * inv;
+    out[2] = (hx[0] * n[1] - hx[1] * n[0] + Emt[2] - Ept[2]) * inv;
+    // E*_t = (Zp Emt + Zm Ept + Zp Zm (Hm - Hp) x n) / (Zm + Zp); F_H = -E*_t x n
+    const Real zz = Zp * Zm;
+    Real et[3] = {(Zp * Emt[0] + Zm * Ept[0] + zz * (dH[1] * n[2] - dH[2] * n[1])) * inv,
+                  (Zp * Emt[1] + Zm * Ept[1] + zz * (dH[2] * n[0] - dH[0] * n[2])) * inv,
+                  (Zp * Emt[2] + Zm * Ept[2] + zz * (dH[0] * n[1] - dH[1] * n[0])) * inv};
+    out[3] = -(et[1] * n[2] - et[2] * n[1]);
+    out[4] = -(et[2] * n[0] - et[0] * n[2]);
+    out[5] = -(et[0] * n[1] - et[1] * n[0]);
+}
+
+// closed-form inverse of G(g) u = (eps E - H x g, mu H + E x g) (Sec. 4), FP64
+__device__ __forceinline__ void ginv_apply(const double w[6], const double g[3], double eps, double mu,
+                                           double out[6]) {
+    const double em = eps * mu;
+    const double s = 1.0 / (em - (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
+    double a[3] = {mu * w[0] + (w[4] * g[2] - w[5] * g[1]), mu * w[1] + (w[5] * g[0] - w[3] * g[2]),
+                   mu * w[2] + (w[3] * g[1] - w[4] * g[0])};
+    double b[3] = {eps * w[3] - (w[1] * g[2] - w[2] * g[1]), eps * w[4] - (w[2] * g[0] - w[0] * g[2]),
+                   eps * w[5] - (w[0] * g[1] - w[1] * g[0])};
+    const double ga = (g[0] * a[0] + g[1] * a[1] + g[2] * a[2]) / em;
+    const double gb = (g[0] * b[0] + g[1] * b[1] + g[2] * b[2]) / em;
+    for (int c = 0; c < 3; ++c) {
+        out[c] = s * (a[c] - g[c] * ga);
+        out[3 + c] = s * (b[c] - g[c] * gb);
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ int field6(int r) {   // index of field r inside (Ex,Ey,Ez,Hx,Hy,Hz)
+    if (DIM == 3) return r;
+    return r == 2 ? 5 : r;
+}
+
+template <typename Real, int DIM, int P>
+__global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_layer_kernel(const KArgs a, int64_t t0) {
+    using Sh = Shape<DIM, P>;
+    constexpr int NF = Sh::NF, NB = Sh::NB, NFB = Sh::NFB, NV = Sh::NV, NT = Sh::NT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemLayout<Real, DIM, P> lay(a.max_patch);
+    Real* sY = (Real*)(smem + lay.off_Y);
+    Real* sUa = (Real*)(smem + lay.off_Ua);
+    Real* sUb = (Real*)(smem + lay.off_Ub);
+    Real* sTr = (Real*)(smem + lay.off_tr);
+    Real* sGi = (Real*)(smem + lay.off_Gi);
+    double* sGphi = (double*)(smem + lay.off_gphi);
+    double* sGdel = (double*)(smem + lay.off_gdel);
+    double* sMat = (double*)(smem + lay.off_mat);
+    Real* sAc = (Real*)(smem + lay.off_ac);
+    Real* sGd = (Real*)(smem + lay.off_gd);
+    Real* sNrm = (Real*)(smem + lay.off_nrm);
+    Real* sLiftc = (Real*)(smem + lay.off_liftc);
+    Real* sTrs = (Real*)(smem + lay.off_trs);
+    Real* sZ = (Real*)(smem + lay.off_Z);
+    int8_t* sJ = (int8_t*)(smem + lay.off_j);
+    int8_t* sNslot = (int8_t*)(smem + lay.off_nslot);
+    int8_t* sNfi = (int8_t*)(smem + lay.off_nfi);
+
+    const Real* S = (const Real*)a.S;
+    const Real* Tr = (const Real*)a.Tr;
+    const Real* Lf = (const Real*)a.L;
+    const int tid = threadIdx.x;
+    const int64_t tent = t0 + blockIdx.x;
+    const int V = a.tent_v[tent];
+    const double tb = a.tent_tb[tent], dt = a.tent_tt[tent] - tb;
+    const int64_t pb = a.patch_ptr[V];
+    const int ns = (int)(a.patch_ptr[V + 1] - pb);
+    Real* state = (Real*)a.state + (int64_t)blockIdx.y * a.rhs_stride;
+    constexpr int ESZ = NF * NB;
+
+    // ---- (a) gather: per-element setup (FP64 geometry) and patch state ----
+    for (int k = tid; k < ns; k += NT) {
+        const int e = a.patch_elem[pb + k];
+        const int8_t* info = a.patch_info + (pb + k) * 12;
+        const int j = info[0];
+        const double* g = a.geo + (int64_t)e * 32;
+        double gp[3] = {0, 0, 0};
+        for (int i = 0; i < NV; ++i) {
+            const double tv = (i == j) ? tb : a.tau[a.elems[(int64_t)e * NV + i]];
+            for (int c = 0; c < 3; ++c) gp[c] += tv * g[3 * i + c];
+        }
+        for (int c = 0; c < 3; ++c) {
+            sGphi[3 * k + c] = gp[c];
+            sGdel[3 * k + c] = dt * g[3 * j + c];
+            sGd[3 * k + c] = (Real)(dt * g[3 * j + c]);
+        }
+        for (int l = 0; l < DIM; ++l)
+            for (int c = 0; c < 3; ++c) sAc[(k * DIM + l) * 3 + c] = (Real)(dt * g[3 * (l + 1) + c]);
+        sMat[2 * k] = g[29];
+        sMat[2 * k + 1] = g[30];
+        sZ[k * (1 + DIM)] = (Real)g[31];
+        sTrs[k] = (Real)g[28];
+        sJ[k] = (int8_t)j;
+        for (int f = 0, fi = 0; f < NV; ++f) {
+            if (f == j) continue;
+            for (int c = 0; c < 3; ++c) sNrm[(k * DIM + fi) * 3 + c] = (Real)g[12 + 3 * f + c];
+            sLiftc[k * DIM + fi] = (Real)(dt * g[24 + f] * g[28]);
+            sNslot[k * DIM + fi] = info[4 + f];
+            ++fi;
+        }
+    }
+    for (int idx = tid; idx < ns * ESZ; idx += NT) {
+        const int k = idx / ESZ, r = idx - k * ESZ;
+        sY[idx] = state[(int64_t)a.patch_elem[pb + k] * ESZ + r];
+    }
+    __syncthreads();
+    // neighbour's facet position (needs the neighbour's j) and impedance
+    for (int k = tid; k < ns; k += NT) {
+        const int8_t* info = a.patch_info + (pb + k) * 12;
+        const int j = sJ[k];
+        for (int f = 0, fi = 0; f < NV; ++f) {
+            if (f == j) continue;
+            const int s2 = info[4 + f];
+            int8_t nfi = -1;
+            Real z2 = sZ[k * (1 + DIM)];
+            if (s2 >= 0) {
+                const int f2 = info[8 + f];
+                nfi = (int8_t)(f2 - (f2 > sJ[s2] ? 1 : 0));
+                z2 = sZ[s2 * (1 + DIM)];
+            }
+            sNfi[k * DIM + fi] = nfi;
+            sZ[k * (1 + DIM) + 1 + fi] = z2;
+            ++fi;
+        }
+    }
+    __syncthreads();
+
+    Real* Ucur = sUa;
+    Real* Unext = sUb;
+    for (int i = 0; i < a.m; ++i) {
+        const double ti = (double)i / (double)a.m;
+        // G(t_i)^-1 per element, FP64 -> state precision
+        for (int k = tid; k < ns; k += NT) {
+            double g[3];
+            for (int c = 0; c < 3; ++c) g[c] = sGphi[3 * k + c] + ti * sGdel[3 * k + c];
+            const double eps = sMat[2 * k], mu = sMat[2 * k + 1];
+            if (!(g[0] * g[0] + g[1] * g[1] + g[2] * g[2] < eps * mu)) atomicExch(a.err, 1);
+            for (int s = 0; s < NF; ++s) {
+                double w[6] = {0, 0, 0, 0, 0, 0}, o[6];
+                w[field6<DIM>(s)] = 1.0;
+                ginv_apply(w, g, eps, mu, o);
+                for (int r = 0; r < NF; ++r) sGi[(k * NF + r) * NF + s] = (Real)o[field6<DIM>(r)];
+            }
+        }
+        __syncthreads();
+        // U_{i,0} = G_i^-1 Y_{i,0}
+        for (int idx = tid; idx < ns * NB; idx += NT) {
+            const int k = idx / NB, b = idx - k * NB;
+            const Real* Gi = sGi + k * NF * NF;
+            Real y[NF];
+            for (int s = 0; s < NF; ++s) y[s] = sY[k * ESZ + s * NB + b];
+            for (int r = 0; r < NF; ++r) {
+                Real acc = 0;
+                for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * y[s];
+                Ucur[k * ESZ + r * NB + b] = acc;
+            }
+        }
+        __syncthreads();
+        for (int n = 1; n <= a.q; ++n) {
+            // ---- (b1) facet traces of U on the facets containing V ----
+            for (int idx = tid; idx < ns * DIM * NFB; idx += NT) {
+                const int k = idx / (DIM * NFB), rem = idx - k * DIM * NFB, fi = rem / NFB, c = rem - fi * NFB;
+                const int j = sJ[k];
+                const int f = fi + (fi >= j ? 1 : 0);
+                const Real* T = Tr + ((size_t)f * NFB + c) * NB;
+                const Real* U = Ucur + k * ESZ;
+                Real acc[NF];
+#pragma unroll
+                for (int s = 0; s < NF; ++s) acc[s] = 0;
+                for (int b = 0; b < NB; ++b) {
+                    const Real t = __ldg(T + b);
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) acc[s] += t * U[s * NB + b];
+                }
+                const Real sc = sTrs[k];
+                Real* out = sTr + ((k * DIM + fi) * NF) * NFB + c;
+#pragma unroll
+                for (int s = 0; s < NF; ++s) out[s * NFB] = acc[s] * sc;
+            }
+            __syncthreads();
+            // ---- (b2) numerical flux, once per facet (lower slot owns an interior facet) ----
+            for (int idx = tid; idx < ns * DIM * NFB; idx += NT) {
+                const int k = idx / (DIM * NFB), rem = idx - k * DIM * NFB, fi = rem / NFB, c = rem - fi * NFB;
+                const int s2 = sNslot[k * DIM + fi];
+                if (s2 >= 0 && s2 < k) continue;
+                Real* mine = sTr + ((k * DIM + fi) * NF) * NFB + c;
+                Real um[6] = {0, 0, 0, 0, 0, 0}, up[6] = {0, 0, 0, 0, 0, 0}, F[6], nrm[3];
+#pragma unroll
+                for (int s = 0; s < NF; ++s) um[field6<DIM>(s)] = mine[s * NFB];
+                Real* other = nullptr;
+                if (s2 >= 0) {
+                    other = sTr + ((s2 * DIM + sNfi[k * DIM + fi]) * NF) * NFB + c;
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) up[field6<DIM>(s)] = other[s * NFB];
+                } else {
+#pragma unroll
+                    for (int s = 0; s < 6; ++s) up[s] = s < 3 ? -um[s] : um[s];
+                }
+                for (int cc = 0; cc < 3; ++cc) nrm[cc] = sNrm[(k * DIM + fi) * 3 + cc];
+                upwind6<Real>(um, up, nrm, sZ[k * (1 + DIM)], sZ[k * (1 + DIM) + 1 + fi], F);
+#pragma unroll
+                for (int s = 0; s < NF; ++s) mine[s * NFB] = F[field6<DIM>(s)];
+                if (other) {
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) other[s * NFB] = -F[field6<DIM>(s)];
+                }
+            }
+            __syncthreads();
+            // ---- (b3)+(c) volume + lift, Taylor accumulation, next U ----
+            const Real cn = (Real)a.taylor[n];
+            const Real nn = (Real)n;
+            for (int idx = tid; idx < ns * NB; idx += NT) {
+                const int k = idx / NB, av = idx - k * NB;
+                const int j = sJ[k];
+                const Real* U = Ucur + k * ESZ;
+                Real Pm[DIM][NF];
+#pragma unroll
+                for (int l = 0; l < DIM; ++l)
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) Pm[l][s] = 0;
+                const Real* Sj = S + ((size_t)j * DIM * NB + av) * NB;
+                for (int b = 0; b < NB; ++b) {
+                    Real sv[DIM];
+#pragma unroll
+                    for (int l = 0; l < DIM; ++l) sv[l] = __ldg(Sj + (size_t)l * NB * NB + b);
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) {
+                        const Real u = U[s * NB + b];
+#pragma unroll
+                        for (int l = 0; l < DIM; ++l) Pm[l][s] += sv[l] * u;
+                    }
+                }
+                Real Yn[NF];
+                const Real* ac = sAc + k * DIM * 3;
+                if constexpr (DIM == 3) {
+                    Real vE[3] = {0, 0, 0}, vH[3] = {0, 0, 0};
+#pragma unroll
+                    for (int l = 0; l < DIM; ++l) {
+                        const Real ax = ac[3 * l], ay = ac[3 * l + 1], az = ac[3 * l + 2];
+                        // -a x P_H
+                        vE[0] -= ay * Pm[l][5] - az * Pm[l][4];
+                        vE[1] -= az * Pm[l][3] - ax * Pm[l][5];
+                        vE[2] -= ax * Pm[l][4] - ay * Pm[l][3];
+                        // a x P_E
+                        vH[0] += ay * Pm[l][2] - az * Pm[l][1];
+                        vH[1] += az * Pm[l][0] - ax * Pm[l][2];
+                        vH[2] += ax * Pm[l][1] - ay * Pm[l][0];
+                    }
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) { Yn[c] = vE[c]; Yn[3 + c] = vH[c]; }
+                } else {
+                    Real ex = 0, ey = 0, hz = 0;
+#pragma unroll
+                    for (int l = 0; l < DIM; ++l) {
+                        const Real ax = ac[3 * l], ay = ac[3 * l + 1];
+                        ex -= ay * Pm[l][2];
+                        ey += ax * Pm[l][2];
+                        hz += ax * Pm[l][1] - ay * Pm[l][0];
+                    }
+                    Yn[0] = ex; Yn[1] = ey; Yn[2] = hz;
+                }
+                // lift of the facet fluxes
+#pragma unroll
+                for (int fi = 0; fi < DIM; ++fi) {
+                    const int f = fi + (fi >= j ? 1 : 0);
+                    const Real* Lr = Lf + (((size_t)j * NV + f) * NB + av) * NFB;
+                    const Real* Fx = sTr + ((k * DIM + fi) * NF) * NFB;
+                    const Real lc = sLiftc[k * DIM + fi];
+                    Real acc[NF];
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) acc[s] = 0;
+                    for (int c = 0; c < NFB; ++c) {
+                        const Real lv = __ldg(Lr + c);
+#pragma unroll
+                        for (int s = 0; s < NF; ++s) acc[s] += lv * Fx[s * NFB + c];
+                    }
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) Yn[s] -= lc * acc[s];
+                }
+                // Taylor accumulation Y_{i+1,0} += (1/m)^n/n! Y_{i,n}
+#pragma unroll
+                for (int s = 0; s < NF; ++s) sY[k * ESZ + s * NB + av] += cn * Yn[s];
+                if (n < a.q) {
+                    // U_{i,n} = G_i^-1 (Y_{i,n} - n M' U_{i,n-1})
+                    const Real* gd = sGd + 3 * k;
+                    Real r6[NF];
+                    if constexpr (DIM == 3) {
+                        const Real E0 = U[0 * NB + av], E1 = U[1 * NB + av], E2 = U[2 * NB + av];
+                        const Real H0 = U[3 * NB + av], H1 = U[4 * NB + av], H2 = U[5 * NB + av];
+                        // M'U = [-H x gd ; E x gd]
+                        r6[0] = Yn[0] + nn * (H1 * gd[2] - H2 * gd[1]);
+                        r6[1] = Yn[1] + nn * (H2 * gd[0] - H0 * gd[2]);
+                        r6[2] = Yn[2] + nn * (H0 * gd[1] - H1 * gd[0]);
+                        r6[3] = Yn[3] - nn * (E1 * gd[2] - E2 * gd[1]);
+                        r6[4] = Yn[4] - nn * (E2 * gd[0] - E0 * gd[2]);
+                        r6[5] = Yn[5] - nn * (E0 * gd[1] - E1 * gd[0]);
+                    } else {
+                        const Real Ex = U[0 * NB + av], Ey = U[1 * NB + av], Hz = U[2 * NB + av];
+                        // M'U (TE) = (Hz gy, -Hz gx, Ex gy - Ey gx)
+                        r6[0] = Yn[0] - nn * (Hz * gd[1]);
+                        r6[1] = Yn[1] + nn * (Hz * gd[0]);
+                        r6[2] = Yn[2] - nn * (Ex * gd[1] - Ey * gd[0]);
+                    }
+                    const Real* Gi = sGi + k * NF * NF;
+#pragma unroll
+                    for (int r = 0; r < NF; ++r) {
+                        Real acc = 0;
+#pragma unroll
+                        for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * r6[s];
+                        Unext[k * ESZ + r * NB + av] = acc;
+                    }
+                }
+            }
+            __syncthreads();
+            Real* tmp = Ucur; Ucur = Unext; Unext = tmp;
+        }
+    }
+    // ---- (d) scatter the tent-top Y; advance the front at V ----
+    bool bad = false;
+    for (int idx = tid; idx < ns * ESZ; idx += NT) {
+        const int k = idx / ESZ, r = idx - k * ESZ;
+        const Real v = sY[idx];
+        if (!isfinite((double)v)) bad = true;
+        state[(int64_t)a.patch_elem[pb + k] * ESZ + r] = v;
+    }
+    if (bad) atomicExch(a.err, 2);
+    if (tid == 0 && blockIdx.y == 0) a.tau[V] = a.tent_tt[tent];
+}
+
+}  // namespace mtp

@@ -1,0 +1,49 @@
+// Launch wrappers for the tent kernels; instantiated per state precision in
+// mtp_k64.cu / mtp_k32.cu so the two halves compile in parallel.
+#pragma once
+
+#include "mtp_kernels.cuh"
+
+namespace mtp {
+
+using LaunchFn = cudaError_t (*)(const KArgs&, int64_t t0, int n_tents, int n_rhs, cudaStream_t st);
+using PrepareFn = cudaError_t (*)(int max_patch, size_t* smem_bytes);
+
+template <typename Real, int DIM, int P>
+cudaError_t prepare_tent_kernel(int max_patch, size_t* smem_bytes) {
+    SmemLayout<Real, DIM, P> lay(max_patch);
+    *smem_bytes = lay.bytes;
+    return cudaFuncSetAttribute(tent_layer_kernel<Real, DIM, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)lay.bytes);
+}
+
+template <typename Real, int DIM, int P>
+cudaError_t launch_tent_kernel(const KArgs& a, int64_t t0, int n_tents, int n_rhs, cudaStream_t st) {
+    SmemLayout<Real, DIM, P> lay(a.max_patch);
+    dim3 grid(n_tents, n_rhs);
+    tent_layer_kernel<Real, DIM, P><<<grid, Shape<DIM, P>::NT, lay.bytes, st>>>(a, t0);
+    return cudaGetLastError();
+}
+
+struct KernelEntry {
+    LaunchFn launch;
+    PrepareFn prepare;
+};
+
+// entries[dim - 2][p - 1]
+void kernel_table_f64(KernelEntry entries[2][4]);
+void kernel_table_f32(KernelEntry entries[2][4]);
+
+#define MTP_KERNEL_TABLE(NAME, REAL)                                                   \
+    void NAME(KernelEntry e[2][4]) {                                                   \
+        e[0][0] = {launch_tent_kernel<REAL, 2, 1>, prepare_tent_kernel<REAL, 2, 1>};   \
+        e[0][1] = {launch_tent_kernel<REAL, 2, 2>, prepare_tent_kernel<REAL, 2, 2>};   \
+        e[0][2] = {launch_tent_kernel<REAL, 2, 3>, prepare_tent_kernel<REAL, 2, 3>};   \
+        e[0][3] = {launch_tent_kernel<REAL, 2, 4>, prepare_tent_kernel<REAL, 2, 4>};   \
+        e[1][0] = {launch_tent_kernel<REAL, 3, 1>, prepare_tent_kernel<REAL, 3, 1>};   \
+        e[1][1] = {launch_tent_kernel<REAL, 3, 2>, prepare_tent_kernel<REAL, 3, 2>};   \
+        e[1][2] = {launch_tent_kernel<REAL, 3, 3>, prepare_tent_kernel<REAL, 3, 3>};   \
+        e[1][3] = {launch_tent_kernel<REAL, 3, 4>, prepare_tent_kernel<REAL, 3, 4>};   \
+    }
+
+}  // namespace mtp

@@ -1,0 +1,87 @@
+"""C-ABI library on the host (no GPU): exported symbols, argument checking, and the
+host tent pitcher against the oracle's pitcher, bit for bit (Sec. 2)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import mtp_synth as S
+import paper_1906_11029_gb300 as mtp
+from oracle.pitch import pitch_tents
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    header = open(os.path.join(ROOT, "include", "mtp.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|void|const char\*)\s+(mtp_\w+)\s*\(", header, re.M))
+    assert declared, "no declarations parsed"
+    lib = ctypes.CDLL(mtp.library_path())
+    missing = [s for s in sorted(declared) if not hasattr(lib, s)]
+    assert not missing, missing
+    assert declared == set(mtp.ABI_SYMBOLS)
+
+
+def test_mesh_errors():
+    v, e = S.square_mesh(2)
+    one = np.ones(len(e))
+    with pytest.raises(mtp.MtpError) as ex:
+        mtp.Mesh(2, v, e, one, one, p=5)
+    assert ex.value.code == mtp.MTP_EUNSUPPORTED
+    bad = e.copy()
+    bad[0] = [0, 1, 2]                           # collinear vertices (0,0), (.5,0), (1,0)
+    with pytest.raises(mtp.MtpError) as ex:
+        mtp.Mesh(2, v, bad, one, one, p=2)
+    assert ex.value.code == mtp.MTP_EMESH
+    with pytest.raises(mtp.MtpError) as ex:
+        mtp.Mesh(2, v, e, -one, one, p=2)
+    assert ex.value.code == mtp.MTP_EINVAL
+    with pytest.raises(mtp.MtpError) as ex:
+        mtp.Mesh(2, v, np.vstack([e, e[:1]]), np.ones(len(e) + 1), np.ones(len(e) + 1), p=2)
+    assert ex.value.code == mtp.MTP_EMESH       # a facet shared by three elements
+    m = mtp.Mesh(2, v, e, one, one, p=2)
+    with pytest.raises(mtp.MtpError) as ex:
+        m.pitch(0.5, causality_factor=1.5)
+    assert ex.value.code == mtp.MTP_EINVAL
+
+
+def test_mesh_info():
+    w = S.cube_mode(3, 3, 0.1)
+    m = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=3)
+    assert m.info == {"dim": 3, "n_fields": 6, "n_basis": 20, "n_elems": 162, "n_verts": 64, "max_patch": 24}
+
+
+def _compare(w, cf=0.5, wavespeed=None):
+    ref = pitch_tents(w.verts, w.elems, w.eps, w.mu, w.T, cf, wavespeed)
+    m = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=1)
+    t = m.pitch(w.T, cf, wavespeed)
+    got = t.get()
+    for k in ("vertex", "layer", "layer_ptr"):
+        assert np.array_equal(got[k], ref[k]), k
+    for k in ("t_bot", "t_top"):
+        assert np.array_equal(got[k].view(np.uint64), ref[k].view(np.uint64)), k   # bit-exact
+    return got
+
+
+@pytest.mark.parametrize("make", [
+    lambda: S.te_square(8, 2, 0.5),                               # 2D TE cavity, 128 triangles
+    lambda: S.Workload("sq_pert", 2, S.perturb_interior(*[S.square_mesh(6)[0]], 1 / 6, 0.2, 3),
+                       S.square_mesh(6)[1], np.ones(72), np.ones(72), 1, 0.3),
+    lambda: S.cube_mode(6, 1, 0.3),                               # perturbed Kuhn cube
+    lambda: S.graded_sphere(n=6, p=1, T=0.2),                     # graded + eps jump
+    lambda: S.adjoint_cube(n=4, p=1, T=0.3),                      # random eps per element
+])
+def test_pitcher_bit_exact_against_oracle(make):
+    _compare(make())
+
+
+def test_pitcher_bit_exact_with_wavespeed():
+    w = S.adjoint_cube(n=3, p=1, T=0.2)
+    _compare(w, cf=0.4, wavespeed=np.ones(len(w.elems)))
+
+
+@pytest.mark.slow
+def test_pitcher_bit_exact_cube16():
+    _compare(S.cube_mode(16, 3, 1.0))

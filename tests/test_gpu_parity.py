@@ -1,0 +1,165 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (GB300).
+
+States are exchanged through lattice values of the conserved variable y (basis
+independent), so the oracle (Bernstein basis, dense LU, exact integrals) and the
+CUDA path (orthonormal basis, closed-form mass inverse) share no arithmetic.
+
+Tolerances (relative L2 over all compared lattice values, per the required
+precision contract): FP64 mode <= 1e-11, FP32 mode <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import mtp_synth as S
+import paper_1906_11029_gb300 as mtp
+from _oracle_bridge import oracle_full_run, oracle_setup, oracle_single_tents, rel_l2
+from oracle.pitch import pitch_tents
+
+pytestmark = pytest.mark.gpu
+TOL = {mtp.MTP_FP64: 1e-11, mtp.MTP_FP32: 1e-5}
+DEV = "cuda:0"
+
+
+def _gpu_full(w, precision, vals0, n_rhs=1, wavespeed=None):
+    m = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=precision, n_rhs=n_rhs)
+    t = m.pitch(w.T, w.causality, wavespeed)
+    v0 = torch.tensor(np.broadcast_to(vals0, (n_rhs,) + vals0.shape).copy(), device=DEV)
+    st = m.state_from_lattice(v0)
+    e0 = m.energy(st)
+    t.evolve(st)
+    out = m.state_to_lattice(st).cpu().numpy()
+    e1 = m.energy(st)
+    torch.cuda.synchronize()
+    return out, e0, e1
+
+
+_CASES = {
+    "te_square_n8_p2": lambda: S.te_square(8, 2, 0.5),            # the 2D TE cavity workload in full
+    "te_square_n4_p1": lambda: S.te_square(4, 1, 0.3),
+    "te_square_n3_p4": lambda: S.te_square(3, 4, 0.15),
+    "cube_n2_p2": lambda: S.cube_mode(2, 2, 0.12),
+    "cube_n2_p3": lambda: S.cube_mode(2, 3, 0.1),
+    "cube_n2_p1": lambda: S.cube_mode(2, 1, 0.15),
+    "graded_n3_p2": lambda: S.graded_sphere(n=3, p=2, T=0.06, width=0.3),   # eps jump + grading
+    "cube_n2_p4": lambda: S.cube_mode(2, 4, 0.04),
+}
+_ORACLE = {}
+
+
+def _oracle(name):
+    if name not in _ORACLE:
+        _ORACLE[name] = oracle_full_run(_CASES[name]())
+    return _ORACLE[name]
+
+
+@pytest.mark.parametrize("precision", [mtp.MTP_FP64, mtp.MTP_FP32])
+@pytest.mark.parametrize("name", list(_CASES))
+def test_full_evolve_matches_oracle(name, precision):
+    w = _CASES[name]()
+    vals0, ref, oe0, oe1 = _oracle(name)
+    out, e0, e1 = _gpu_full(w, precision, vals0)
+    err = rel_l2(out[0], ref)
+    assert err <= TOL[precision], (name, precision, err)
+    assert abs(e0[0] - oe0) <= 10 * TOL[precision] * oe0
+    assert abs(e1[0] - oe1) <= 10 * TOL[precision] * oe1
+    assert e1[0] <= e0[0] * (1 + 1e-12 if precision == mtp.MTP_FP64 else 1 + 1e-5)
+
+
+def test_multi_rhs_equals_single():
+    w = S.cube_mode(2, 2, 0.12)
+    vals0, _, _, _ = _oracle("cube_n2_p2")
+    rng = np.random.default_rng(5)
+    stack = np.stack([vals0, rng.standard_normal(vals0.shape), 0.5 * vals0])
+    m = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=2, n_rhs=3)
+    t = m.pitch(w.T)
+    st = m.state_from_lattice(torch.tensor(stack, device=DEV))
+    t.evolve(st)
+    many = m.state_to_lattice(st).cpu().numpy()
+    for r in range(3):
+        one, _, _ = _gpu_full(w, mtp.MTP_FP64, stack[r])
+        assert np.array_equal(one[0], many[r])
+
+
+def test_fp64_deterministic_and_host_entry_point():
+    w = S.cube_mode(2, 3, 0.1)
+    vals0, _, _, _ = _oracle("cube_n2_p3")
+    a, _, _ = _gpu_full(w, mtp.MTP_FP64, vals0)
+    b, _, _ = _gpu_full(w, mtp.MTP_FP64, vals0)
+    assert np.array_equal(a, b)
+    m = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=3)
+    t = m.pitch(w.T)
+    st = m.state_from_lattice(torch.tensor(vals0[None], device=DEV))
+    host_in = st.cpu().numpy().copy()
+    host_out = np.empty_like(host_in)
+    t.evolve_host(host_in, host_out)
+    t.evolve(st)
+    assert np.array_equal(host_out, st.cpu().numpy())
+
+
+def test_lattice_roundtrip_and_T_mismatch():
+    w = S.graded_sphere(n=3, p=4, T=0.05)
+    m = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=4)
+    v = torch.tensor(np.random.default_rng(1).standard_normal(m.lattice_shape), device=DEV)
+    back = m.state_to_lattice(m.state_from_lattice(v))
+    assert rel_l2(back.cpu().numpy(), v.cpu().numpy()) < 1e-12
+    t = m.pitch(w.T)
+    with pytest.raises(mtp.MtpError) as ex:
+        mtp.mtp_evolve(t.h, m.new_state(), w.T * 2)
+    assert ex.value.code == mtp.MTP_EINVAL
+
+
+def _single_layer_check(w, precision, layer_frac, n_sample, seed):
+    """Full-size workload, the launch configuration of a real evolve: one layer applied to a
+    seeded random state on the GPU; the oracle recomputes a sample of that layer's tents."""
+    m = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=precision)
+    t = m.pitch(w.T, w.causality)
+    tents = t.get()
+    L = int(layer_frac * (len(tents["layer_ptr"]) - 1))
+    vals = np.random.default_rng(seed).standard_normal(m.lattice_shape[1:])
+    st = m.state_from_lattice(torch.tensor(vals[None], device=DEV))
+    t.evolve_layers(st, L, L + 1)
+    out = m.state_to_lattice(st).cpu().numpy()[0]
+    lp = tents["layer_ptr"]
+    idx = np.arange(lp[L], lp[L + 1])
+    sample = np.random.default_rng(seed + 1).choice(idx, size=min(n_sample, len(idx)), replace=False)
+    disc = oracle_setup(w)
+    ref = oracle_single_tents(w, disc, tents, L, vals, sample)
+    errs = []
+    for tt, r in ref.items():
+        patch = disc.mesh.patch[int(tents["vertex"][tt])]
+        errs.append(rel_l2(out[patch], r))
+    # elements outside the layer's patches are untouched
+    touched = np.zeros(len(w.elems), bool)
+    for tt in idx:
+        touched[disc.mesh.patch[int(tents["vertex"][tt])]] = True
+    assert rel_l2(out[~touched], vals[~touched]) < (1e-14 if precision == mtp.MTP_FP64 else 1e-7)
+    return max(errs)
+
+
+@pytest.mark.parametrize("precision", [mtp.MTP_FP64, mtp.MTP_FP32])
+def test_cube16_p3_single_layer_sampled(precision):
+    """3D cavity workload at full size (16^3 x 6 perturbed tets, p = 3, T = 1)."""
+    w = S.cube_mode(16, 3, 1.0)
+    err = _single_layer_check(w, precision, 0.5, 6, 101)
+    assert err <= TOL[precision], err
+
+
+@pytest.mark.parametrize("precision", [mtp.MTP_FP64, mtp.MTP_FP32])
+def test_graded32_p4_single_layer_sampled(precision):
+    """Graded 32^3 x 6 tets, p = 4, eps = 4 ball (full size of the mixed-precision workload)."""
+    w = S.graded_sphere(32, 4, 0.5)
+    err = _single_layer_check(w, precision, 0.3, 3, 202)
+    assert err <= TOL[precision], err
+
+
+def test_pitcher_on_device_box_matches_oracle():
+    w = S.cube_mode(8, 2, 0.4)
+    ref = pitch_tents(w.verts, w.elems, w.eps, w.mu, w.T, 0.5)
+    got = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=2).pitch(w.T).get()
+    for k in ("vertex", "layer", "layer_ptr"):
+        assert np.array_equal(got[k], ref[k])
+    assert np.array_equal(got["t_top"].view(np.uint64), ref["t_top"].view(np.uint64))
