@@ -33,6 +33,10 @@ import numpy as np  # noqa: E402
 
 FP32_SM_LANES = 128            # FP32 FMA lanes per SM (Blackwell)
 N_SMS = 152
+# DRAM bytes (read + write) per tent of the FP32 p=4 tent kernel from the last ncu capture of
+# the current kernel version (profiles/tent_layer_kernel_fp32_p4_graded32.md); None once the
+# kernel has changed since the counters were taken.
+TRAFFIC_BYTES_PER_TENT = {"fp32": 27452.0}
 
 
 def load_peaks():
@@ -117,11 +121,12 @@ class Clocks:
 
 def cpu_baseline_sample(workload, n_tents, seed=7):
     """Time the FP64 oracle (test infrastructure, as it stands) on a bounded sample of the
-    workload: the first n_tents tents of layer 0 from a seeded random state on the flat front.
+    workload: the first n_tents tents (in layer order, from the flat front t = 0) applied to a
+    seeded random state.
     Runs in a child process pinned to one BLAS thread; returns the JSON it prints."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", workload,
-                        "--cpu-tents", str(n_tents), "--seed", str(seed)],
+                        "--cpu-tents", str(n_tents), "--seed", str(seed), "--cpu-rounds", "80"],
                        capture_output=True, text=True, env=env, cwd=ROOT)
     if r.returncode != 0:
         return {"error": r.stderr[-400:]}
@@ -131,22 +136,26 @@ def cpu_baseline_sample(workload, n_tents, seed=7):
 def cpu_worker(args):
     from oracle.mesh import Mesh as OMesh
     from oracle.mtp import Discretization
-    from oracle.pitch import pitch_first_round
+    from oracle.pitch import pitch_tents
     w = make_workload(args.cpu_worker)
     disc = Discretization(OMesh(w.verts, w.elems, w.eps, w.mu), w.p)
-    first = pitch_first_round(w.verts, w.elems, w.eps, w.mu, w.T, w.causality)
+    tents = pitch_tents(w.verts, w.elems, w.eps, w.mu, w.T, w.causality, max_rounds=args.cpu_rounds)
     rng = np.random.default_rng(args.seed)
+    Y = rng.standard_normal((len(w.elems), disc.nf * disc.nb))
     tau = np.zeros(len(w.verts))
-    done, dofs = 0, 0.0
+    n = min(args.cpu_tents, len(tents["vertex"]))
+    dofs = 0.0
     t0 = time.perf_counter()
-    for V, tb, tt in first[: args.cpu_tents]:
+    for t in range(n):                    # (layer, vertex) order: any prefix respects the DAG
+        V = int(tents["vertex"][t])
+        tb, tt = float(tents["t_bot"][t]), float(tents["t_top"][t])
         patch = disc.mesh.patch[V]
-        Yp = rng.standard_normal((len(patch), disc.nf * disc.nb))
-        disc.sat_tent(V, tt - tb, tau, Yp)
-        done += 1
+        slots, Yp = disc.sat_tent(V, tt - tb, tau, Y[patch])
+        Y[slots] = Yp
+        tau[V] = tt
         dofs += len(patch) * disc.nf * disc.nb * (2 * w.p) * (w.p + 1)
     dt = time.perf_counter() - t0
-    print(json.dumps({"value": dofs / dt, "seconds": dt, "tents": done, "dofs": dofs}))
+    print(json.dumps({"value": dofs / dt, "seconds": dt, "tents": n, "dofs": dofs}))
 
 
 def run_reference(args):
@@ -168,12 +177,30 @@ def run_reference(args):
         "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "elems": int(len(w.elems)), "p": w.p,
-                   "sample": f"{args.ref_tents} tents of layer 0 per step, seeded random state"},
+                   "sample": f"first {args.ref_tents} tents (layer order) per step, seeded random state"},
         "cpu_baseline": {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.ref_tents} tents of layer 0 per step"},
+                         "sample": f"first {args.ref_tents} tents (layer order) per step"},
         "e2e": {"value": rate, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
+
+
+def run_profile(args):
+    """Profiling driver: build the workload, then apply layers [a, b) once (no timing)."""
+    import torch
+    import paper_1906_11029_gb300 as mtp
+    a, b = (int(x) for x in args.profile_window.split(":"))
+    w = make_workload(args.workload)
+    prec = mtp.MTP_FP32 if args.precision == "fp32" else mtp.MTP_FP64
+    mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=prec)
+    tents = mesh.pitch(w.T, w.causality)
+    state = mesh.state_from_lattice(torch.tensor(initial_lattice(w)[None], device="cuda"))
+    if a > 0:
+        tents.evolve_layers(state, 0, a)
+    tents.evolve_layers(state, a, b)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_window": [a, b], "launches": int(np.count_nonzero(
+        np.diff(tents.get()["layer_ptr"][a:b + 1]))), "workload": w.name}))
 
 
 def run_mtp(args):
@@ -251,8 +278,10 @@ def run_mtp(args):
         peak = args.fp64_peak_tflops
         bound = "alu"
     achieved = flops_per_launch / (launch_ms / 1e3) / 1e12
+    tpl = TRAFFIC_BYTES_PER_TENT.get(args.precision) if args.workload == "graded" else None
+    traffic = None if tpl is None else tpl * tents.info["n_tents"] / launches_per_step
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": f"tent_layer_kernel<{args.precision},3,{w.p}>",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)"}
 
@@ -261,7 +290,7 @@ def run_mtp(args):
     h_out = torch.empty_like(h_in).pin_memory()
     tents.evolve_host(h_in, h_out)
     torch.cuda.synchronize()
-    e2e_steps = max(1, min(args.steps, 2))
+    e2e_steps = 1
     barrier()
     te0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -307,7 +336,7 @@ def run_mtp(args):
     if rank == 0 and not args.no_cpu_baseline:
         r = cpu_baseline_sample(args.workload, args.cpu_tents)
         cpu = {"value": r.get("value"), "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"first {r.get('tents')} tents of layer 0 of the same workload, seeded random "
+               "sample": f"first {r.get('tents')} tents (layer order) of the same workload, seeded random "
                          f"state, FP64 numpy oracle, {r.get('seconds', 0):.1f} s", **({"error": r["error"]} if "error" in r else {})}
 
     if rank == 0:
@@ -333,23 +362,27 @@ def run_mtp(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mtp", choices=["mtp", "reference"])
     ap.add_argument("--workload", default="graded", choices=["graded", "cube", "small"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--fp64-window", type=float, default=0.02)
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
-    ap.add_argument("--cpu-tents", type=int, default=12)
+    ap.add_argument("--cpu-tents", type=int, default=80)
+    ap.add_argument("--cpu-rounds", type=int, default=80)
     ap.add_argument("--ref-tents", type=int, default=6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", default=None)
+    ap.add_argument("--profile-window", default=None, help="a:b -> apply layers [a, b) once and exit")
     ap.add_argument("--seed", type=int, default=7)
     args = ap.parse_args()
     if args.cpu_worker:
         return cpu_worker(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_window:
+        return run_profile(args)
     return run_mtp(args)
 
 
