@@ -121,11 +121,14 @@ int mtp_state_to_lattice(mtp_mesh_t mesh, const void* state_dev, double* vals_de
  * q-stage SAT over m sub-intervals (Sec. 4, eqs. coeff_rec and recursion-init), with
  * the mass solve in the closed form of Sec. 4.  All tents of a layer (times n_rhs)
  * run in one kernel launch; the layers are replayed from a CUDA graph.  T must equal
- * the pitched T (MTP_EINVAL otherwise).  Asynchronous on the stream. */
+ * the pitched T (MTP_EINVAL otherwise).  Returns after the work has completed on the
+ * stream: the device-side error word is read back (MTP_ECAUSAL if a tent violated
+ * causality, MTP_ENUMERIC on a non-finite result). */
 int mtp_evolve(mtp_tents_t tents, void* state_dev, double T, void* stream);
 
 /* Apply only layers [layer_begin, layer_end) to a state that sits on the front just
- * before layer_begin (each vertex at the top of its last earlier tent). */
+ * before layer_begin (each vertex at the top of its last earlier tent).  Completion and
+ * errors as for mtp_evolve. */
 int mtp_evolve_layers(mtp_tents_t tents, void* state_dev, int64_t layer_begin,
                       int64_t layer_end, void* stream);
 

@@ -60,6 +60,16 @@ static int upload(T** dst, const T* src, size_t n) {
     return MTP_OK;
 }
 
+// rows of `cols` entries -> rows of pad4(cols) entries, zeros in the pad (16-byte vector reads)
+static std::vector<double> pad_rows(const std::vector<double>& src, int cols) {
+    const int pc = pad4(cols);
+    const size_t rows = src.size() / cols;
+    std::vector<double> out(rows * pc, 0.0);
+    for (size_t r = 0; r < rows; ++r)
+        for (int c = 0; c < cols; ++c) out[r * pc + c] = src[r * cols + c];
+    return out;
+}
+
 static int upload_real(const Mesh& m, void** dst, const std::vector<double>& src) {
     if (m.precision == MTP_FP64) return upload((double**)dst, src.data(), src.size());
     std::vector<float> f(src.begin(), src.end());
@@ -87,9 +97,9 @@ int device_mesh_upload(Mesh& m) {
     MTP_TRY(upload(&d.patch_ptr, m.patch_ptr.data(), m.patch_ptr.size()));
     MTP_TRY(upload(&d.patch_elem, m.patch_elem.data(), m.patch_elem.size()));
     MTP_TRY(upload(&d.patch_info, m.patch_info.data(), m.patch_info.size()));
-    MTP_TRY(upload_real(m, &d.S, m.ref.S));
-    MTP_TRY(upload_real(m, &d.Tr, m.ref.Tr));
-    MTP_TRY(upload_real(m, &d.L, m.ref.L));
+    MTP_TRY(upload_real(m, &d.S, pad_rows(m.ref.S, m.nb)));     // [j][l][a][NBP]
+    MTP_TRY(upload_real(m, &d.Tr, pad_rows(m.ref.Tr, m.nb)));   // [f][c][NBP]
+    MTP_TRY(upload_real(m, &d.L, pad_rows(m.ref.L, m.nfb)));    // [j][f][a][NFBP]
     MTP_TRY(upload(&d.V, m.ref.V.data(), m.ref.V.size()));
     MTP_TRY(upload(&d.Vinv, m.ref.Vinv.data(), m.ref.Vinv.size()));
     CUDA_TRY(cudaMalloc((void**)&d.partial, sizeof(double) * (kEnergyBlocks + 1) * m.n_rhs));

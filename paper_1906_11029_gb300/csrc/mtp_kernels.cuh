@@ -20,6 +20,11 @@
 //            Y[a] -= dt (d-1)!|F| / sqrt|det J| sum_c L[j][f][a][c] F*[c].
 //   mass:    U = G(t_i)^-1 Y per coefficient (6x6, closed form of Sec. 4, built in FP64)
 //            M' U = [-H x dt grad(lambda_j) ; E x dt grad(lambda_j)].
+//
+// Memory layout for the SIMT contractions: every table row and every shared-memory
+// coefficient row is padded to a multiple of 4 entries (zeros in the pad) and read as
+// 16-byte vectors; a thread owns two basis functions (or two facet modes), so each
+// vector of U read from shared memory feeds 2 x 3 x 6 FMAs per entry.
 #pragma once
 
 #include <cstdint>
@@ -39,9 +44,9 @@ struct KArgs {
     const int32_t* elems;       // [ne][dim+1] sorted vertex ids
     const double* geo;          // [ne][32]
     double* tau;                // vertex times of the current front
-    const void* S;              // reference tables in the state precision
-    const void* Tr;
-    const void* L;
+    const void* S;              // [j][l][a][NBP]  reference tables in the state precision,
+    const void* Tr;             // [f][c][NBP]     rows padded with zeros (see pad4)
+    const void* L;              // [j][f][a][NFBP]
     void* state;                // [rhs][ne][nf][nb]
     int64_t rhs_stride;         // ne * nf * nb
     int* err;                   // error word (0 = ok, 1 = causality, 2 = non-finite)
@@ -50,13 +55,35 @@ struct KArgs {
     double taylor[kMaxTaylor];  // (1/m)^n / n!
 };
 
+__host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
+
 template <int DIM, int P>
 struct Shape {
     static constexpr int NF = DIM == 2 ? 3 : 6;
     static constexpr int NB = DIM == 2 ? (P + 1) * (P + 2) / 2 : (P + 1) * (P + 2) * (P + 3) / 6;
     static constexpr int NFB = DIM == 2 ? P + 1 : (P + 1) * (P + 2) / 2;
+    static constexpr int NBP = pad4(NB);
+    static constexpr int NFBP = pad4(NFB);
     static constexpr int NV = DIM + 1;
     static constexpr int NT = DIM == 2 ? 128 : 256;   // threads per CTA
+    static constexpr int AP = 2;                       // basis functions per thread
+    static constexpr int NAG = (NB + AP - 1) / AP;     // basis groups per element
+    static constexpr int NCG = (NFB + AP - 1) / AP;    // facet-mode groups per facet
+};
+
+template <typename Real>
+struct Vec;
+template <>
+struct Vec<float> {
+    using T = float4;
+    static constexpr int W = 4;
+    static __device__ __forceinline__ void get(const T& v, float o[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+};
+template <>
+struct Vec<double> {
+    using T = double2;
+    static constexpr int W = 2;
+    static __device__ __forceinline__ void get(const T& v, double o[2]) { o[0] = v.x; o[1] = v.y; }
 };
 
 // shared-memory carve-up, sizes from the mesh's largest patch
@@ -65,14 +92,15 @@ struct SmemLayout {
     using Sh = Shape<DIM, P>;
     static __host__ __device__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
     size_t off_Y, off_Ua, off_Ub, off_tr, off_Gi, off_gphi, off_gdel, off_mat, off_ac, off_gd, off_nrm,
-        off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, bytes;
+        off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, bytes, state_bytes, tr_bytes;
     __host__ __device__ explicit SmemLayout(int mp) {
         size_t o = 0;
-        const size_t state = (size_t)mp * Sh::NF * Sh::NB * sizeof(Real);
-        off_Y = o; o = align16(o + state);
-        off_Ua = o; o = align16(o + state);
-        off_Ub = o; o = align16(o + state);
-        off_tr = o; o = align16(o + (size_t)mp * DIM * Sh::NF * Sh::NFB * sizeof(Real));
+        state_bytes = (size_t)mp * Sh::NF * Sh::NBP * sizeof(Real);
+        tr_bytes = (size_t)mp * DIM * Sh::NF * Sh::NFBP * sizeof(Real);
+        off_Y = o; o = align16(o + state_bytes);
+        off_Ua = o; o = align16(o + state_bytes);
+        off_Ub = o; o = align16(o + state_bytes);
+        off_tr = o; o = align16(o + tr_bytes);
         off_Gi = o; o = align16(o + (size_t)mp * Sh::NF * Sh::NF * sizeof(Real));
         off_gphi = o; o = align16(o + (size_t)mp * 3 * sizeof(double));
         off_gdel = o; o = align16(o + (size_t)mp * 3 * sizeof(double));
@@ -145,7 +173,12 @@ __device__ __forceinline__ int field6(int r) {   // index of field r inside (Ex,
 template <typename Real, int DIM, int P>
 __global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_layer_kernel(const KArgs a, int64_t t0) {
     using Sh = Shape<DIM, P>;
+    using VT = typename Vec<Real>::T;
     constexpr int NF = Sh::NF, NB = Sh::NB, NFB = Sh::NFB, NV = Sh::NV, NT = Sh::NT;
+    constexpr int NBP = Sh::NBP, NFBP = Sh::NFBP, AP = Sh::AP, NAG = Sh::NAG, NCG = Sh::NCG;
+    constexpr int W = Vec<Real>::W;
+    constexpr int ESZ = NF * NBP;           // padded coefficients per element in shared memory
+    constexpr int TSZ = DIM * NF * NFBP;    // padded facet coefficients per element
     extern __shared__ __align__(16) unsigned char smem[];
     const SmemLayout<Real, DIM, P> lay(a.max_patch);
     Real* sY = (Real*)(smem + lay.off_Y);
@@ -176,7 +209,6 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_layer_kernel(const KAr
     const int64_t pb = a.patch_ptr[V];
     const int ns = (int)(a.patch_ptr[V + 1] - pb);
     Real* state = (Real*)a.state + (int64_t)blockIdx.y * a.rhs_stride;
-    constexpr int ESZ = NF * NB;
 
     // ---- (a) gather: per-element setup (FP64 geometry) and patch state ----
     for (int k = tid; k < ns; k += NT) {
@@ -209,10 +241,14 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_layer_kernel(const KAr
             ++fi;
         }
     }
+    // state rows (pads zero); U buffers and facet buffers zeroed so their pads stay zero
     for (int idx = tid; idx < ns * ESZ; idx += NT) {
-        const int k = idx / ESZ, r = idx - k * ESZ;
-        sY[idx] = state[(int64_t)a.patch_elem[pb + k] * ESZ + r];
+        const int k = idx / ESZ, r = idx - k * ESZ, s = r / NBP, b = r - s * NBP;
+        sY[idx] = b < NB ? state[((int64_t)a.patch_elem[pb + k] * NF + s) * NB + b] : Real(0);
+        sUa[idx] = Real(0);
+        sUb[idx] = Real(0);
     }
+    for (int idx = tid; idx < ns * TSZ; idx += NT) sTr[idx] = Real(0);
     __syncthreads();
     // neighbour's facet position (needs the neighbour's j) and impedance
     for (int k = tid; k < ns; k += NT) {
@@ -258,34 +294,56 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_layer_kernel(const KAr
             const int k = idx / NB, b = idx - k * NB;
             const Real* Gi = sGi + k * NF * NF;
             Real y[NF];
-            for (int s = 0; s < NF; ++s) y[s] = sY[k * ESZ + s * NB + b];
+#pragma unroll
+            for (int s = 0; s < NF; ++s) y[s] = sY[k * ESZ + s * NBP + b];
+#pragma unroll
             for (int r = 0; r < NF; ++r) {
                 Real acc = 0;
+#pragma unroll
                 for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * y[s];
-                Ucur[k * ESZ + r * NB + b] = acc;
+                Ucur[k * ESZ + r * NBP + b] = acc;
             }
         }
         __syncthreads();
         for (int n = 1; n <= a.q; ++n) {
-            // ---- (b1) facet traces of U on the facets containing V ----
-            for (int idx = tid; idx < ns * DIM * NFB; idx += NT) {
-                const int k = idx / (DIM * NFB), rem = idx - k * DIM * NFB, fi = rem / NFB, c = rem - fi * NFB;
+            // ---- (b1) facet traces of U on the facets containing V (two modes per thread) ----
+            for (int idx = tid; idx < ns * DIM * NCG; idx += NT) {
+                const int k = idx / (DIM * NCG), rem = idx - k * DIM * NCG, fi = rem / NCG;
+                const int c0 = (rem - fi * NCG) * AP;
                 const int j = sJ[k];
                 const int f = fi + (fi >= j ? 1 : 0);
-                const Real* T = Tr + ((size_t)f * NFB + c) * NB;
                 const Real* U = Ucur + k * ESZ;
-                Real acc[NF];
+                const Real* T0 = Tr + ((size_t)f * NFB + c0) * NBP;
+                const bool two = c0 + 1 < NFB;
+                const Real* T1 = two ? T0 + NBP : T0;
+                Real acc[AP][NF];
 #pragma unroll
-                for (int s = 0; s < NF; ++s) acc[s] = 0;
-                for (int b = 0; b < NB; ++b) {
-                    const Real t = __ldg(T + b);
+                for (int ci = 0; ci < AP; ++ci)
 #pragma unroll
-                    for (int s = 0; s < NF; ++s) acc[s] += t * U[s * NB + b];
+                    for (int s = 0; s < NF; ++s) acc[ci][s] = 0;
+#pragma unroll 1
+                for (int b = 0; b < NBP; b += W) {
+                    Real t0v[W], t1v[W];
+                    Vec<Real>::get(__ldg((const VT*)(T0 + b)), t0v);
+                    Vec<Real>::get(__ldg((const VT*)(T1 + b)), t1v);
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) {
+                        Real u[W];
+                        Vec<Real>::get(*(const VT*)(U + s * NBP + b), u);
+#pragma unroll
+                        for (int v = 0; v < W; ++v) {
+                            acc[0][s] += t0v[v] * u[v];
+                            acc[1][s] += t1v[v] * u[v];
+                        }
+                    }
                 }
                 const Real sc = sTrs[k];
-                Real* out = sTr + ((k * DIM + fi) * NF) * NFB + c;
+                Real* out = sTr + k * TSZ + fi * NF * NFBP + c0;
 #pragma unroll
-                for (int s = 0; s < NF; ++s) out[s * NFB] = acc[s] * sc;
+                for (int s = 0; s < NF; ++s) {
+                    out[s * NFBP] = acc[0][s] * sc;
+                    if (two) out[s * NFBP + 1] = acc[1][s] * sc;
+                }
             }
             __syncthreads();
             // ---- (b2) numerical flux, once per facet (lower slot owns an interior facet) ----
@@ -293,131 +351,169 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_layer_kernel(const KAr
                 const int k = idx / (DIM * NFB), rem = idx - k * DIM * NFB, fi = rem / NFB, c = rem - fi * NFB;
                 const int s2 = sNslot[k * DIM + fi];
                 if (s2 >= 0 && s2 < k) continue;
-                Real* mine = sTr + ((k * DIM + fi) * NF) * NFB + c;
+                Real* mine = sTr + k * TSZ + fi * NF * NFBP + c;
                 Real um[6] = {0, 0, 0, 0, 0, 0}, up[6] = {0, 0, 0, 0, 0, 0}, F[6], nrm[3];
 #pragma unroll
-                for (int s = 0; s < NF; ++s) um[field6<DIM>(s)] = mine[s * NFB];
+                for (int s = 0; s < NF; ++s) um[field6<DIM>(s)] = mine[s * NFBP];
                 Real* other = nullptr;
                 if (s2 >= 0) {
-                    other = sTr + ((s2 * DIM + sNfi[k * DIM + fi]) * NF) * NFB + c;
+                    other = sTr + s2 * TSZ + sNfi[k * DIM + fi] * NF * NFBP + c;
 #pragma unroll
-                    for (int s = 0; s < NF; ++s) up[field6<DIM>(s)] = other[s * NFB];
+                    for (int s = 0; s < NF; ++s) up[field6<DIM>(s)] = other[s * NFBP];
                 } else {
 #pragma unroll
                     for (int s = 0; s < 6; ++s) up[s] = s < 3 ? -um[s] : um[s];
                 }
                 for (int cc = 0; cc < 3; ++cc) nrm[cc] = sNrm[(k * DIM + fi) * 3 + cc];
                 upwind6<Real>(um, up, nrm, sZ[k * (1 + DIM)], sZ[k * (1 + DIM) + 1 + fi], F);
+                const Real lc = sLiftc[k * DIM + fi];
 #pragma unroll
-                for (int s = 0; s < NF; ++s) mine[s * NFB] = F[field6<DIM>(s)];
+                for (int s = 0; s < NF; ++s) mine[s * NFBP] = lc * F[field6<DIM>(s)];
                 if (other) {
+                    const Real lc2 = sLiftc[s2 * DIM + sNfi[k * DIM + fi]];
 #pragma unroll
-                    for (int s = 0; s < NF; ++s) other[s * NFB] = -F[field6<DIM>(s)];
+                    for (int s = 0; s < NF; ++s) other[s * NFBP] = -lc2 * F[field6<DIM>(s)];
                 }
             }
             __syncthreads();
-            // ---- (b3)+(c) volume + lift, Taylor accumulation, next U ----
+            // ---- (b3)+(c) volume + lift, Taylor accumulation, next U (two basis functions) ----
             const Real cn = (Real)a.taylor[n];
             const Real nn = (Real)n;
-            for (int idx = tid; idx < ns * NB; idx += NT) {
-                const int k = idx / NB, av = idx - k * NB;
+            for (int idx = tid; idx < ns * NAG; idx += NT) {
+                const int k = idx / NAG, a0 = (idx - k * NAG) * AP;
+                const bool two = a0 + 1 < NB;
                 const int j = sJ[k];
                 const Real* U = Ucur + k * ESZ;
-                Real Pm[DIM][NF];
+                Real Pm[AP][DIM][NF];
 #pragma unroll
-                for (int l = 0; l < DIM; ++l)
+                for (int ai = 0; ai < AP; ++ai)
 #pragma unroll
-                    for (int s = 0; s < NF; ++s) Pm[l][s] = 0;
-                const Real* Sj = S + ((size_t)j * DIM * NB + av) * NB;
-                for (int b = 0; b < NB; ++b) {
-                    Real sv[DIM];
+                    for (int l = 0; l < DIM; ++l)
 #pragma unroll
-                    for (int l = 0; l < DIM; ++l) sv[l] = __ldg(Sj + (size_t)l * NB * NB + b);
+                        for (int s = 0; s < NF; ++s) Pm[ai][l][s] = 0;
+                const Real* S0 = S + ((size_t)j * DIM * NB + a0) * NBP;
+                const Real* S1 = two ? S0 + NBP : S0;
+#pragma unroll 1
+                for (int b = 0; b < NBP; b += W) {
+                    Real sv[AP][DIM][W];
+#pragma unroll
+                    for (int l = 0; l < DIM; ++l) {
+                        Vec<Real>::get(__ldg((const VT*)(S0 + (size_t)l * NB * NBP + b)), sv[0][l]);
+                        Vec<Real>::get(__ldg((const VT*)(S1 + (size_t)l * NB * NBP + b)), sv[1][l]);
+                    }
 #pragma unroll
                     for (int s = 0; s < NF; ++s) {
-                        const Real u = U[s * NB + b];
+                        Real u[W];
+                        Vec<Real>::get(*(const VT*)(U + s * NBP + b), u);
 #pragma unroll
-                        for (int l = 0; l < DIM; ++l) Pm[l][s] += sv[l] * u;
+                        for (int v = 0; v < W; ++v)
+#pragma unroll
+                            for (int ai = 0; ai < AP; ++ai)
+#pragma unroll
+                                for (int l = 0; l < DIM; ++l) Pm[ai][l][s] += sv[ai][l][v] * u[v];
                     }
                 }
-                Real Yn[NF];
+                Real Yn[AP][NF];
                 const Real* ac = sAc + k * DIM * 3;
-                if constexpr (DIM == 3) {
-                    Real vE[3] = {0, 0, 0}, vH[3] = {0, 0, 0};
 #pragma unroll
-                    for (int l = 0; l < DIM; ++l) {
-                        const Real ax = ac[3 * l], ay = ac[3 * l + 1], az = ac[3 * l + 2];
-                        // -a x P_H
-                        vE[0] -= ay * Pm[l][5] - az * Pm[l][4];
-                        vE[1] -= az * Pm[l][3] - ax * Pm[l][5];
-                        vE[2] -= ax * Pm[l][4] - ay * Pm[l][3];
-                        // a x P_E
-                        vH[0] += ay * Pm[l][2] - az * Pm[l][1];
-                        vH[1] += az * Pm[l][0] - ax * Pm[l][2];
-                        vH[2] += ax * Pm[l][1] - ay * Pm[l][0];
+                for (int ai = 0; ai < AP; ++ai) {
+                    if constexpr (DIM == 3) {
+                        Real vE[3] = {0, 0, 0}, vH[3] = {0, 0, 0};
+#pragma unroll
+                        for (int l = 0; l < DIM; ++l) {
+                            const Real ax = ac[3 * l], ay = ac[3 * l + 1], az = ac[3 * l + 2];
+                            const Real* Pl = Pm[ai][l];
+                            vE[0] -= ay * Pl[5] - az * Pl[4];   // -a x P_H
+                            vE[1] -= az * Pl[3] - ax * Pl[5];
+                            vE[2] -= ax * Pl[4] - ay * Pl[3];
+                            vH[0] += ay * Pl[2] - az * Pl[1];   //  a x P_E
+                            vH[1] += az * Pl[0] - ax * Pl[2];
+                            vH[2] += ax * Pl[1] - ay * Pl[0];
+                        }
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) { Yn[ai][c] = vE[c]; Yn[ai][3 + c] = vH[c]; }
+                    } else {
+                        Real ex = 0, ey = 0, hz = 0;
+#pragma unroll
+                        for (int l = 0; l < DIM; ++l) {
+                            const Real ax = ac[3 * l], ay = ac[3 * l + 1];
+                            const Real* Pl = Pm[ai][l];
+                            ex -= ay * Pl[2];
+                            ey += ax * Pl[2];
+                            hz += ax * Pl[1] - ay * Pl[0];
+                        }
+                        Yn[ai][0] = ex; Yn[ai][1] = ey; Yn[ai][2] = hz;
                     }
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) { Yn[c] = vE[c]; Yn[3 + c] = vH[c]; }
-                } else {
-                    Real ex = 0, ey = 0, hz = 0;
-#pragma unroll
-                    for (int l = 0; l < DIM; ++l) {
-                        const Real ax = ac[3 * l], ay = ac[3 * l + 1];
-                        ex -= ay * Pm[l][2];
-                        ey += ax * Pm[l][2];
-                        hz += ax * Pm[l][1] - ay * Pm[l][0];
-                    }
-                    Yn[0] = ex; Yn[1] = ey; Yn[2] = hz;
                 }
-                // lift of the facet fluxes
+                // lift of the (already dt (d-1)!|F|/sqrt|det J|-scaled) facet fluxes
 #pragma unroll
                 for (int fi = 0; fi < DIM; ++fi) {
                     const int f = fi + (fi >= j ? 1 : 0);
-                    const Real* Lr = Lf + (((size_t)j * NV + f) * NB + av) * NFB;
-                    const Real* Fx = sTr + ((k * DIM + fi) * NF) * NFB;
-                    const Real lc = sLiftc[k * DIM + fi];
-                    Real acc[NF];
+                    const Real* L0 = Lf + (((size_t)j * NV + f) * NB + a0) * NFBP;
+                    const Real* L1 = two ? L0 + NFBP : L0;
+                    const Real* Fx = sTr + k * TSZ + fi * NF * NFBP;
+                    Real acc[AP][NF];
 #pragma unroll
-                    for (int s = 0; s < NF; ++s) acc[s] = 0;
-                    for (int c = 0; c < NFB; ++c) {
-                        const Real lv = __ldg(Lr + c);
+                    for (int ai = 0; ai < AP; ++ai)
 #pragma unroll
-                        for (int s = 0; s < NF; ++s) acc[s] += lv * Fx[s * NFB + c];
+                        for (int s = 0; s < NF; ++s) acc[ai][s] = 0;
+#pragma unroll
+                    for (int c = 0; c < NFBP; c += W) {
+                        Real l0[W], l1[W];
+                        Vec<Real>::get(__ldg((const VT*)(L0 + c)), l0);
+                        Vec<Real>::get(__ldg((const VT*)(L1 + c)), l1);
+#pragma unroll
+                        for (int s = 0; s < NF; ++s) {
+                            Real fv[W];
+                            Vec<Real>::get(*(const VT*)(Fx + s * NFBP + c), fv);
+#pragma unroll
+                            for (int v = 0; v < W; ++v) {
+                                acc[0][s] += l0[v] * fv[v];
+                                acc[1][s] += l1[v] * fv[v];
+                            }
+                        }
                     }
 #pragma unroll
-                    for (int s = 0; s < NF; ++s) Yn[s] -= lc * acc[s];
+                    for (int ai = 0; ai < AP; ++ai)
+#pragma unroll
+                        for (int s = 0; s < NF; ++s) Yn[ai][s] -= acc[ai][s];
                 }
-                // Taylor accumulation Y_{i+1,0} += (1/m)^n/n! Y_{i,n}
+                const Real* gd = sGd + 3 * k;
+                const Real* Gi = sGi + k * NF * NF;
 #pragma unroll
-                for (int s = 0; s < NF; ++s) sY[k * ESZ + s * NB + av] += cn * Yn[s];
-                if (n < a.q) {
-                    // U_{i,n} = G_i^-1 (Y_{i,n} - n M' U_{i,n-1})
-                    const Real* gd = sGd + 3 * k;
-                    Real r6[NF];
-                    if constexpr (DIM == 3) {
-                        const Real E0 = U[0 * NB + av], E1 = U[1 * NB + av], E2 = U[2 * NB + av];
-                        const Real H0 = U[3 * NB + av], H1 = U[4 * NB + av], H2 = U[5 * NB + av];
-                        // M'U = [-H x gd ; E x gd]
-                        r6[0] = Yn[0] + nn * (H1 * gd[2] - H2 * gd[1]);
-                        r6[1] = Yn[1] + nn * (H2 * gd[0] - H0 * gd[2]);
-                        r6[2] = Yn[2] + nn * (H0 * gd[1] - H1 * gd[0]);
-                        r6[3] = Yn[3] - nn * (E1 * gd[2] - E2 * gd[1]);
-                        r6[4] = Yn[4] - nn * (E2 * gd[0] - E0 * gd[2]);
-                        r6[5] = Yn[5] - nn * (E0 * gd[1] - E1 * gd[0]);
-                    } else {
-                        const Real Ex = U[0 * NB + av], Ey = U[1 * NB + av], Hz = U[2 * NB + av];
-                        // M'U (TE) = (Hz gy, -Hz gx, Ex gy - Ey gx)
-                        r6[0] = Yn[0] - nn * (Hz * gd[1]);
-                        r6[1] = Yn[1] + nn * (Hz * gd[0]);
-                        r6[2] = Yn[2] - nn * (Ex * gd[1] - Ey * gd[0]);
-                    }
-                    const Real* Gi = sGi + k * NF * NF;
+                for (int ai = 0; ai < AP; ++ai) {
+                    if (ai == 1 && !two) break;
+                    const int av = a0 + ai;
+                    // Taylor accumulation Y_{i+1,0} += (1/m)^n/n! Y_{i,n}
 #pragma unroll
-                    for (int r = 0; r < NF; ++r) {
-                        Real acc = 0;
+                    for (int s = 0; s < NF; ++s) sY[k * ESZ + s * NBP + av] += cn * Yn[ai][s];
+                    if (n < a.q) {
+                        // U_{i,n} = G_i^-1 (Y_{i,n} - n M' U_{i,n-1})
+                        Real r6[NF];
+                        if constexpr (DIM == 3) {
+                            const Real E0 = U[0 * NBP + av], E1 = U[1 * NBP + av], E2 = U[2 * NBP + av];
+                            const Real H0 = U[3 * NBP + av], H1 = U[4 * NBP + av], H2 = U[5 * NBP + av];
+                            // M'U = [-H x gd ; E x gd]
+                            r6[0] = Yn[ai][0] + nn * (H1 * gd[2] - H2 * gd[1]);
+                            r6[1] = Yn[ai][1] + nn * (H2 * gd[0] - H0 * gd[2]);
+                            r6[2] = Yn[ai][2] + nn * (H0 * gd[1] - H1 * gd[0]);
+                            r6[3] = Yn[ai][3] - nn * (E1 * gd[2] - E2 * gd[1]);
+                            r6[4] = Yn[ai][4] - nn * (E2 * gd[0] - E0 * gd[2]);
+                            r6[5] = Yn[ai][5] - nn * (E0 * gd[1] - E1 * gd[0]);
+                        } else {
+                            const Real Ex = U[0 * NBP + av], Ey = U[1 * NBP + av], Hz = U[2 * NBP + av];
+                            // M'U (TE) = (Hz gy, -Hz gx, Ex gy - Ey gx)
+                            r6[0] = Yn[ai][0] - nn * (Hz * gd[1]);
+                            r6[1] = Yn[ai][1] + nn * (Hz * gd[0]);
+                            r6[2] = Yn[ai][2] - nn * (Ex * gd[1] - Ey * gd[0]);
+                        }
 #pragma unroll
-                        for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * r6[s];
-                        Unext[k * ESZ + r * NB + av] = acc;
+                        for (int r = 0; r < NF; ++r) {
+                            Real acc = 0;
+#pragma unroll
+                            for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * r6[s];
+                            Unext[k * ESZ + r * NBP + av] = acc;
+                        }
                     }
                 }
             }
@@ -427,11 +523,11 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_layer_kernel(const KAr
     }
     // ---- (d) scatter the tent-top Y; advance the front at V ----
     bool bad = false;
-    for (int idx = tid; idx < ns * ESZ; idx += NT) {
-        const int k = idx / ESZ, r = idx - k * ESZ;
-        const Real v = sY[idx];
+    for (int idx = tid; idx < ns * NF * NB; idx += NT) {
+        const int k = idx / (NF * NB), r = idx - k * NF * NB, s = r / NB, b = r - s * NB;
+        const Real v = sY[k * ESZ + s * NBP + b];
         if (!isfinite((double)v)) bad = true;
-        state[(int64_t)a.patch_elem[pb + k] * ESZ + r] = v;
+        state[(int64_t)a.patch_elem[pb + k] * NF * NB + r] = v;
     }
     if (bad) atomicExch(a.err, 2);
     if (tid == 0 && blockIdx.y == 0) a.tau[V] = a.tent_tt[tent];
