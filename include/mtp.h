@@ -143,6 +143,24 @@ int mtp_evolve_host(mtp_tents_t tents, const void* state_in_host, void* state_ou
  * Synchronises the stream. */
 int mtp_energy(mtp_mesh_t mesh, const void* state_dev, double* out_host, void* stream);
 
+/* Energy of flat-front states, like mtp_energy, for callers that cannot allocate device
+ * memory when they need it (for example a host framework that owns all device memory
+ * through its own allocator and budget, or a loop that must not allocate after start-up).
+ * The paper has no counterpart to this call.
+ * Inputs and outputs are all the caller's: state_dev (library layout, n_rhs states of
+ * n_elems elements of degree p in the given precision), eps_dev and mu_dev [n_elems]
+ * (double, device), out_dev[n_rhs] (double, device) receives the energies.  Nothing is
+ * allocated: the reduction scratch is a fixed static device array of 304 x 64 doubles
+ * (152 KiB) that every GPU loading this library holds until the process exits; n_rhs
+ * above 64 is rejected with MTP_EINVAL.  Every call writes all the scratch it reads, so
+ * no clearing is needed, but all calls share that one array: calls that overlap on the
+ * GPU (e.g. on two streams at once) race and give wrong results.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  Asynchronous on the stream. */
+int mtp_energy_noalloc(const void* state_dev, const double* eps_dev, const double* mu_dev,
+                       int dim, int64_t n_elems, int p, int precision, int n_rhs,
+                       double* out_dev, void* stream);
+
 /* Thread-local description of the last error returned on this thread. */
 const char* mtp_last_error(void);
 

@@ -28,7 +28,7 @@ _CODES = {0: "MTP_OK", -1: "MTP_EINVAL", -2: "MTP_EMESH", -3: "MTP_ECAUSAL", -4:
 ABI_SYMBOLS = ["mtp_mesh_create", "mtp_mesh_destroy", "mtp_mesh_info", "mtp_pitch_tents",
                "mtp_tents_destroy", "mtp_tents_info", "mtp_tents_get", "mtp_state_from_lattice",
                "mtp_state_to_lattice", "mtp_evolve", "mtp_evolve_layers", "mtp_evolve_host",
-               "mtp_energy", "mtp_last_error"]
+               "mtp_energy", "mtp_energy_noalloc", "mtp_last_error"]
 
 
 class MtpError(RuntimeError):
@@ -62,6 +62,7 @@ def _load():
         "mtp_evolve_layers": (C.c_int, [P, P, I64, I64, P]),
         "mtp_evolve_host": (C.c_int, [P, P, P, D, P]),
         "mtp_energy": (C.c_int, [P, P, P, P]),
+        "mtp_energy_noalloc": (C.c_int, [P, P, P, C.c_int, I64, C.c_int, C.c_int, C.c_int, P, P]),
         "mtp_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -179,6 +180,12 @@ def mtp_energy(mesh, state_dev, n_rhs=1, stream=None):
     out = np.zeros(n_rhs, np.float64)
     _check(_lib.mtp_energy(mesh, _ptr(state_dev), _ptr(out), _stream(stream)))
     return out
+
+
+def mtp_energy_noalloc(state_dev, eps_dev, mu_dev, dim, n_elems, p, precision, n_rhs, out_dev, stream=None):
+    """Energies into the caller's device buffer out_dev[n_rhs]; allocates nothing (see mtp.h)."""
+    _check(_lib.mtp_energy_noalloc(_ptr(state_dev), _ptr(eps_dev), _ptr(mu_dev), dim, n_elems, p, precision,
+                                   n_rhs, _ptr(out_dev), _stream(stream)))
 
 
 # ------------------------------------------------------------------------ convenience wrappers
