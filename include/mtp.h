@@ -138,6 +138,22 @@ int mtp_evolve_layers(mtp_tents_t tents, void* state_dev, int64_t layer_begin,
 int mtp_evolve_host(mtp_tents_t tents, const void* state_in_host, void* state_out_host,
                     double T, void* stream);
 
+/* Discrete adjoint of mtp_evolve (not in the paper): the reverse-in-time sweep through the
+ * tent maps.  Given state0_dev (the state at t = 0) and lambda_T_dev = dJ/dY(T) for a
+ * functional J of the final state (both library layout, dev), writes lambda_0_dev =
+ * dJ/dY(0) and dJ_deps_dev, dJ_dmu_dev [n_elems] (double, dev, overwritten, summed over the
+ * right-hand sides) = the derivatives of J through the tent maps' dependence on eps and mu
+ * (the mass operator g(u) - f(u) grad(phi) and the facet impedances).  Dependence of the
+ * initial state or of J on eps, mu is the caller's to add.  The forward pass keeps the state
+ * before every checkpoint_every-th layer (0: about sqrt(n_layers)); each segment is
+ * recomputed from its checkpoint and reversed layer by layer, one CTA per tent, replaying
+ * the tent's SAT stages into a device tape.  Device work buffers are owned by the tents
+ * handle.  Completion and errors as for mtp_evolve; MTP_EUNSUPPORTED if the adjoint kernel's
+ * shared memory for this degree and patch size exceeds the device limit. */
+int mtp_adjoint(mtp_tents_t tents, const void* state0_dev, const void* lambda_T_dev,
+                void* lambda_0_dev, double* dJ_deps_dev, double* dJ_dmu_dev,
+                int64_t checkpoint_every, void* stream);
+
 /* Electromagnetic energy of a state on a flat front, per right-hand side:
  * out_host[r] = 1/2 sum_T int_T (|y_E|^2 / eps + |y_H|^2 / mu)  (= 1/2 int eps|E|^2 + mu|H|^2).
  * Synchronises the stream. */

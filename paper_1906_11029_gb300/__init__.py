@@ -28,7 +28,7 @@ _CODES = {0: "MTP_OK", -1: "MTP_EINVAL", -2: "MTP_EMESH", -3: "MTP_ECAUSAL", -4:
 ABI_SYMBOLS = ["mtp_mesh_create", "mtp_mesh_destroy", "mtp_mesh_info", "mtp_pitch_tents",
                "mtp_tents_destroy", "mtp_tents_info", "mtp_tents_get", "mtp_state_from_lattice",
                "mtp_state_to_lattice", "mtp_evolve", "mtp_evolve_layers", "mtp_evolve_host",
-               "mtp_energy", "mtp_energy_noalloc", "mtp_last_error"]
+               "mtp_adjoint", "mtp_energy", "mtp_energy_noalloc", "mtp_last_error"]
 
 
 class MtpError(RuntimeError):
@@ -61,6 +61,7 @@ def _load():
         "mtp_evolve": (C.c_int, [P, P, D, P]),
         "mtp_evolve_layers": (C.c_int, [P, P, I64, I64, P]),
         "mtp_evolve_host": (C.c_int, [P, P, P, D, P]),
+        "mtp_adjoint": (C.c_int, [P, P, P, P, P, P, I64, P]),
         "mtp_energy": (C.c_int, [P, P, P, P]),
         "mtp_energy_noalloc": (C.c_int, [P, P, P, C.c_int, I64, C.c_int, C.c_int, C.c_int, P, P]),
         "mtp_last_error": (C.c_char_p, []),
@@ -176,6 +177,11 @@ def mtp_evolve_host(tents, state_in, state_out, T, stream=None):
     _check(_lib.mtp_evolve_host(tents, _ptr(state_in), _ptr(state_out), T, _stream(stream)))
 
 
+def mtp_adjoint(tents, state0_dev, lam_T_dev, lam_0_dev, geps_dev, gmu_dev, checkpoint_every=0, stream=None):
+    _check(_lib.mtp_adjoint(tents, _ptr(state0_dev), _ptr(lam_T_dev), _ptr(lam_0_dev), _ptr(geps_dev),
+                            _ptr(gmu_dev), checkpoint_every, _stream(stream)))
+
+
 def mtp_energy(mesh, state_dev, n_rhs=1, stream=None):
     out = np.zeros(n_rhs, np.float64)
     _check(_lib.mtp_energy(mesh, _ptr(state_dev), _ptr(out), _stream(stream)))
@@ -264,3 +270,40 @@ class Tents:
         if getattr(self, "h", None):
             mtp_tents_destroy(self.h)
             self.h = None
+
+
+def _torch_function():
+    import torch
+
+    class MtpEvolveFunction(torch.autograd.Function):
+        """Y_T = evolve(Y_0) with gradients w.r.t. Y_0 and the per-element eps, mu of the tents'
+        mesh, computed by the reverse sweep mtp_adjoint (tent-layer checkpointing with
+        recomputation).  ``eps``/``mu`` must hold the mesh's values; they are inputs only so
+        that autograd routes their gradients."""
+
+        @staticmethod
+        def forward(ctx, Y0, eps, mu, tents, checkpoint_every=0):
+            YT = Y0.detach().clone().contiguous()
+            tents.evolve(YT)
+            ctx.save_for_backward(Y0.detach().contiguous())
+            ctx.tents = tents
+            ctx.k = checkpoint_every
+            return YT
+
+        @staticmethod
+        def backward(ctx, gYT):
+            (Y0,) = ctx.saved_tensors
+            t = ctx.tents
+            lam0 = torch.empty_like(Y0)
+            ne = t.mesh.info["n_elems"]
+            geps = torch.empty(ne, dtype=torch.float64, device=Y0.device)
+            gmu = torch.empty(ne, dtype=torch.float64, device=Y0.device)
+            mtp_adjoint(t.h, Y0, gYT.contiguous().to(Y0.dtype), lam0, geps, gmu, ctx.k)
+            return lam0, geps, gmu, None, None
+
+    return MtpEvolveFunction
+
+
+def mtp_evolve_autograd(Y0, eps, mu, tents, checkpoint_every=0):
+    """Differentiable evolve (see MtpEvolveFunction)."""
+    return _torch_function().apply(Y0, eps, mu, tents, checkpoint_every)

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 
+#include "mtp_adjoint.cuh"
 #include "mtp_internal.h"
 #include "mtp_launch.cuh"
 
@@ -46,6 +47,10 @@ struct DeviceTents {
     cudaStream_t capture = nullptr;
     cudaGraphExec_t exec = nullptr;
     void* graph_state = nullptr;  // state pointer baked into the graph
+    // adjoint work buffers (grown on demand)
+    void* adj_buf = nullptr;
+    size_t adj_bytes = 0;
+    double* tau_rev = nullptr;
 };
 
 constexpr int kEnergyBlocks = 304;
@@ -121,7 +126,7 @@ void device_tents_free(Tents& t) {
     DeviceTents& d = *t.dev;
     if (d.exec) cudaGraphExecDestroy(d.exec);
     if (d.capture) cudaStreamDestroy(d.capture);
-    void* ptrs[] = {d.v, d.tb, d.tt, d.tau, d.err, d.host_state};
+    void* ptrs[] = {d.v, d.tb, d.tt, d.tau, d.err, d.host_state, d.adj_buf, d.tau_rev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (d.err_host) cudaFreeHost(d.err_host);
@@ -343,6 +348,15 @@ static int check_error_word(Tents& t, cudaStream_t st) {
     return MTP_OK;
 }
 
+// front before layer lb (each vertex at the top of its last earlier tent) -> dst (device)
+static int set_front(Tents& t, int64_t lb, double* dst, cudaStream_t st) {
+    std::vector<double> tau(t.mesh->nv, 0.0);
+    for (int64_t i = 0; i < t.layer_ptr[lb]; ++i) tau[t.vertex[i]] = std::fmax(tau[t.vertex[i]], t.t_top[i]);
+    CUDA_TRY(cudaMemcpyAsync(dst, tau.data(), sizeof(double) * t.mesh->nv, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaStreamSynchronize(st));   // the host vector goes out of scope
+    return MTP_OK;
+}
+
 int device_evolve(Tents& t, void* state, int64_t lb, int64_t le, bool use_graph, void* stream) {
     MTP_TRY(device_tents_upload(t));
     Mesh& m = *t.mesh;
@@ -358,10 +372,7 @@ int device_evolve(Tents& t, void* state, int64_t lb, int64_t le, bool use_graph,
         return set_error(MTP_EUNSUPPORTED, "tent kernel needs " + std::to_string(smem) +
                                                " bytes of shared memory per block; the device allows " +
                                                std::to_string(smem_max));
-    // front before layer lb
-    std::vector<double> tau(m.nv, 0.0);
-    for (int64_t i = 0; i < t.layer_ptr[lb]; ++i) tau[t.vertex[i]] = std::fmax(tau[t.vertex[i]], t.t_top[i]);
-    CUDA_TRY(cudaMemcpyAsync(d.tau, tau.data(), sizeof(double) * m.nv, cudaMemcpyHostToDevice, st));
+    MTP_TRY(set_front(t, lb, d.tau, st));
     CUDA_TRY(cudaMemsetAsync(d.err, 0, sizeof(int), st));
     KArgs a;
     fill_args(t, state, a);
@@ -397,6 +408,105 @@ int device_evolve_host(Tents& t, const void* in, void* out, void* stream) {
     CUDA_TRY(cudaMemcpyAsync(out, d.host_state, bytes, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
     return MTP_OK;
+}
+
+}  // namespace mtp
+
+namespace mtp {
+
+// Reverse sweep with layer checkpointing: the forward pass keeps the state before every
+// K-th layer; each segment is recomputed from its checkpoint (keeping the state before each
+// of its layers) and then reversed layer by layer with the adjoint tent kernel.
+int device_adjoint(Tents& t, const void* state0, const void* lamT, void* lam0, double* geps, double* gmu,
+                   int64_t K, void* stream) {
+    MTP_TRY(device_tents_upload(t));
+    Mesh& m = *t.mesh;
+    DeviceTents& d = *t.dev;
+    cudaStream_t st = (cudaStream_t)stream;
+    static AdjEntry table[2][2][4];
+    static bool init = false;
+    if (!init) { adjoint_table(table); init = true; }
+    const AdjEntry& ae = table[m.precision == MTP_FP64 ? 0 : 1][m.dim - 2][m.p - 1];
+    const KernelEntry& ke = kernel_entry(m);
+    size_t smem = 0, smem_f = 0;
+    CUDA_TRY(ae.prepare(m.max_patch, &smem));
+    CUDA_TRY(ke.prepare(m.max_patch, &smem_f));
+    int dev, smem_max;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if ((int64_t)smem > smem_max)
+        return set_error(MTP_EUNSUPPORTED, "adjoint tent kernel needs " + std::to_string(smem) +
+                                               " bytes of shared memory per block; the device allows " +
+                                               std::to_string(smem_max));
+    const int64_t nl = (int64_t)t.layer_ptr.size() - 1;
+    if (K <= 0) K = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)nl)));
+    K = std::min(K, nl);
+    const int64_t nck = (nl + K - 1) / K;
+    const size_t sbytes = (size_t)m.n_rhs * m.ne * m.nf * m.nb * real_size(m);
+    int64_t max_tents = 0;
+    for (int64_t l = 0; l < nl; ++l) max_tents = std::max(max_tents, t.layer_ptr[l + 1] - t.layer_ptr[l]);
+    const int64_t tstride = ae.tape_stride(m.max_patch, m.m, m.q);
+    const size_t tape_bytes = (size_t)max_tents * m.n_rhs * tstride * real_size(m);
+    const size_t need = (size_t)(nck + K) * sbytes + tape_bytes + 256;
+    if (d.adj_bytes < need) {
+        if (d.adj_buf) cudaFree(d.adj_buf);
+        d.adj_buf = nullptr;
+        d.adj_bytes = 0;
+        CUDA_TRY(cudaMalloc(&d.adj_buf, need));
+        d.adj_bytes = need;
+    }
+    if (!d.tau_rev) CUDA_TRY(cudaMalloc((void**)&d.tau_rev, sizeof(double) * m.nv));
+    auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+    char* base = (char*)d.adj_buf;
+    auto ckpt = [&](int64_t c) { return (void*)(base + c * sbytes); };
+    char* segb = base + nck * sbytes;
+    auto seg = [&](int64_t s) { return (void*)(segb + s * sbytes); };
+    void* tape = (void*)(base + align((size_t)(nck + K) * sbytes));
+
+    CUDA_TRY(cudaMemsetAsync(d.err, 0, sizeof(int), st));
+    // forward pass with checkpoints
+    MTP_TRY(set_front(t, 0, d.tau, st));
+    CUDA_TRY(cudaMemcpyAsync(seg(0), state0, sbytes, cudaMemcpyDeviceToDevice, st));
+    KArgs fa;
+    for (int64_t c = 0; c < nck; ++c) {
+        CUDA_TRY(cudaMemcpyAsync(ckpt(c), seg(0), sbytes, cudaMemcpyDeviceToDevice, st));
+        fill_args(t, seg(0), fa);
+        MTP_TRY(enqueue_layers(t, fa, c * K, std::min((c + 1) * K, nl), st));
+    }
+    // reverse sweep
+    CUDA_TRY(cudaMemcpyAsync(lam0, lamT, sbytes, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(geps, 0, sizeof(double) * m.ne, st));
+    CUDA_TRY(cudaMemsetAsync(gmu, 0, sizeof(double) * m.ne, st));
+    {
+        std::vector<double> top(m.nv, t.T);
+        CUDA_TRY(cudaMemcpyAsync(d.tau_rev, top.data(), sizeof(double) * m.nv, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    AdjArgs aa;
+    for (int64_t c = nck - 1; c >= 0; --c) {
+        const int64_t l0 = c * K, l1 = std::min((c + 1) * K, nl);
+        MTP_TRY(set_front(t, l0, d.tau, st));
+        CUDA_TRY(cudaMemcpyAsync(seg(0), ckpt(c), sbytes, cudaMemcpyDeviceToDevice, st));
+        for (int64_t l = l0; l + 1 < l1; ++l) {
+            CUDA_TRY(cudaMemcpyAsync(seg(l - l0 + 1), seg(l - l0), sbytes, cudaMemcpyDeviceToDevice, st));
+            fill_args(t, seg(l - l0 + 1), fa);
+            MTP_TRY(enqueue_layers(t, fa, l, l + 1, st));
+        }
+        for (int64_t l = l1 - 1; l >= l0; --l) {
+            const int64_t t0 = t.layer_ptr[l], n = t.layer_ptr[l + 1] - t0;
+            if (n == 0) continue;
+            fill_args(t, nullptr, aa.k);
+            aa.k.tau = d.tau_rev;
+            aa.ybot = seg(l - l0);
+            aa.lam = lam0;
+            aa.geps = geps;
+            aa.gmu = gmu;
+            aa.tape = tape;
+            aa.tape_stride = tstride;
+            CUDA_TRY(ae.launch(aa, t0, (int)n, m.n_rhs, st));
+        }
+    }
+    return check_error_word(t, st);
 }
 
 }  // namespace mtp

@@ -534,6 +534,15 @@ int mtp_evolve_host(mtp_tents_t tents, const void* in, void* out, double T, void
     MTP_GUARD_END
 }
 
+int mtp_adjoint(mtp_tents_t tents, const void* state0, const void* lamT, void* lam0, double* geps, double* gmu,
+                int64_t checkpoint_every, void* stream) {
+    MTP_GUARD_BEGIN
+    if (!tents || !state0 || !lamT || !lam0 || !geps || !gmu) return set_error(MTP_EINVAL, "NULL argument");
+    if (checkpoint_every < 0) return set_error(MTP_EINVAL, "checkpoint_every must be >= 0");
+    return device_adjoint(tents->t, state0, lamT, lam0, geps, gmu, checkpoint_every, stream);
+    MTP_GUARD_END
+}
+
 int mtp_energy(mtp_mesh_t mesh, const void* state, double* out_host, void* stream) {
     MTP_GUARD_BEGIN
     if (!mesh || !state || !out_host) return set_error(MTP_EINVAL, "NULL argument");

@@ -89,5 +89,7 @@ int device_evolve(Tents& t, void* state, int64_t layer_begin, int64_t layer_end,
                   void* stream);
 int device_evolve_host(Tents& t, const void* in, void* out, void* stream);
 int device_energy(Mesh& m, const void* state, double* out_host, void* stream);
+int device_adjoint(Tents& t, const void* state0, const void* lamT, void* lam0, double* geps, double* gmu,
+                   int64_t checkpoint_every, void* stream);
 
 }  // namespace mtp

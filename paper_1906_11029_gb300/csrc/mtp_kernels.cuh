@@ -170,367 +170,446 @@ __device__ __forceinline__ int field6(int r) {   // index of field r inside (Ex,
     return r == 2 ? 5 : r;
 }
 
+// Per-CTA view of one tent: shared-memory buffers and tent scalars.
 template <typename Real, int DIM, int P>
-__global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_layer_kernel(const KArgs a, int64_t t0) {
+struct TentCtx {
     using Sh = Shape<DIM, P>;
-    using VT = typename Vec<Real>::T;
-    constexpr int NF = Sh::NF, NB = Sh::NB, NFB = Sh::NFB, NV = Sh::NV, NT = Sh::NT;
-    constexpr int NBP = Sh::NBP, NFBP = Sh::NFBP, AP = Sh::AP, NAG = Sh::NAG, NCG = Sh::NCG;
-    constexpr int W = Vec<Real>::W;
-    constexpr int ESZ = NF * NBP;           // padded coefficients per element in shared memory
-    constexpr int TSZ = DIM * NF * NFBP;    // padded facet coefficients per element
-    extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout<Real, DIM, P> lay(a.max_patch);
-    Real* sY = (Real*)(smem + lay.off_Y);
-    Real* sUa = (Real*)(smem + lay.off_Ua);
-    Real* sUb = (Real*)(smem + lay.off_Ub);
-    Real* sTr = (Real*)(smem + lay.off_tr);
-    Real* sGi = (Real*)(smem + lay.off_Gi);
-    double* sGphi = (double*)(smem + lay.off_gphi);
-    double* sGdel = (double*)(smem + lay.off_gdel);
-    double* sMat = (double*)(smem + lay.off_mat);
-    Real* sAc = (Real*)(smem + lay.off_ac);
-    Real* sGd = (Real*)(smem + lay.off_gd);
-    Real* sNrm = (Real*)(smem + lay.off_nrm);
-    Real* sLiftc = (Real*)(smem + lay.off_liftc);
-    Real* sTrs = (Real*)(smem + lay.off_trs);
-    Real* sZ = (Real*)(smem + lay.off_Z);
-    int8_t* sJ = (int8_t*)(smem + lay.off_j);
-    int8_t* sNslot = (int8_t*)(smem + lay.off_nslot);
-    int8_t* sNfi = (int8_t*)(smem + lay.off_nfi);
+    Real *sY, *sUa, *sUb, *sTr, *sGi;
+    double *sGphi, *sGdel, *sMat;
+    Real *sAc, *sGd, *sNrm, *sLiftc, *sTrs, *sZ;
+    int8_t *sJ, *sNslot, *sNfi;
+    int V, ns;
+    int64_t pb;
+    double tb, dt;
 
-    const Real* S = (const Real*)a.S;
-    const Real* Tr = (const Real*)a.Tr;
-    const Real* Lf = (const Real*)a.L;
+    __device__ void carve(unsigned char* smem, const SmemLayout<Real, DIM, P>& lay) {
+        sY = (Real*)(smem + lay.off_Y);
+        sUa = (Real*)(smem + lay.off_Ua);
+        sUb = (Real*)(smem + lay.off_Ub);
+        sTr = (Real*)(smem + lay.off_tr);
+        sGi = (Real*)(smem + lay.off_Gi);
+        sGphi = (double*)(smem + lay.off_gphi);
+        sGdel = (double*)(smem + lay.off_gdel);
+        sMat = (double*)(smem + lay.off_mat);
+        sAc = (Real*)(smem + lay.off_ac);
+        sGd = (Real*)(smem + lay.off_gd);
+        sNrm = (Real*)(smem + lay.off_nrm);
+        sLiftc = (Real*)(smem + lay.off_liftc);
+        sTrs = (Real*)(smem + lay.off_trs);
+        sZ = (Real*)(smem + lay.off_Z);
+        sJ = (int8_t*)(smem + lay.off_j);
+        sNslot = (int8_t*)(smem + lay.off_nslot);
+        sNfi = (int8_t*)(smem + lay.off_nfi);
+    }
+};
+
+// (a) gather: per-element setup from FP64 geometry and the current front; patch state of
+// `src` into sY (pads zero); U and facet buffers zeroed so their pads stay zero.
+template <typename Real, int DIM, int P>
+__device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t tent, const Real* src) {
+    using Sh = Shape<DIM, P>;
+    constexpr int NF = Sh::NF, NB = Sh::NB, NV = Sh::NV, NT = Sh::NT, NBP = Sh::NBP;
+    constexpr int ESZ = NF * NBP, TSZ = DIM * NF * Sh::NFBP;
     const int tid = threadIdx.x;
-    const int64_t tent = t0 + blockIdx.x;
-    const int V = a.tent_v[tent];
-    const double tb = a.tent_tb[tent], dt = a.tent_tt[tent] - tb;
-    const int64_t pb = a.patch_ptr[V];
-    const int ns = (int)(a.patch_ptr[V + 1] - pb);
-    Real* state = (Real*)a.state + (int64_t)blockIdx.y * a.rhs_stride;
-
-    // ---- (a) gather: per-element setup (FP64 geometry) and patch state ----
+    c.V = a.tent_v[tent];
+    c.tb = a.tent_tb[tent];
+    c.dt = a.tent_tt[tent] - c.tb;
+    c.pb = a.patch_ptr[c.V];
+    c.ns = (int)(a.patch_ptr[c.V + 1] - c.pb);
+    const int ns = c.ns;
+    const double dt = c.dt;
     for (int k = tid; k < ns; k += NT) {
-        const int e = a.patch_elem[pb + k];
-        const int8_t* info = a.patch_info + (pb + k) * 12;
+        const int e = a.patch_elem[c.pb + k];
+        const int8_t* info = a.patch_info + (c.pb + k) * 12;
         const int j = info[0];
         const double* g = a.geo + (int64_t)e * 32;
         double gp[3] = {0, 0, 0};
         for (int i = 0; i < NV; ++i) {
-            const double tv = (i == j) ? tb : a.tau[a.elems[(int64_t)e * NV + i]];
-            for (int c = 0; c < 3; ++c) gp[c] += tv * g[3 * i + c];
+            const double tv = (i == j) ? c.tb : a.tau[a.elems[(int64_t)e * NV + i]];
+            for (int q = 0; q < 3; ++q) gp[q] += tv * g[3 * i + q];
         }
-        for (int c = 0; c < 3; ++c) {
-            sGphi[3 * k + c] = gp[c];
-            sGdel[3 * k + c] = dt * g[3 * j + c];
-            sGd[3 * k + c] = (Real)(dt * g[3 * j + c]);
+        for (int q = 0; q < 3; ++q) {
+            c.sGphi[3 * k + q] = gp[q];
+            c.sGdel[3 * k + q] = dt * g[3 * j + q];
+            c.sGd[3 * k + q] = (Real)(dt * g[3 * j + q]);
         }
         for (int l = 0; l < DIM; ++l)
-            for (int c = 0; c < 3; ++c) sAc[(k * DIM + l) * 3 + c] = (Real)(dt * g[3 * (l + 1) + c]);
-        sMat[2 * k] = g[29];
-        sMat[2 * k + 1] = g[30];
-        sZ[k * (1 + DIM)] = (Real)g[31];
-        sTrs[k] = (Real)g[28];
-        sJ[k] = (int8_t)j;
+            for (int q = 0; q < 3; ++q) c.sAc[(k * DIM + l) * 3 + q] = (Real)(dt * g[3 * (l + 1) + q]);
+        c.sMat[2 * k] = g[29];
+        c.sMat[2 * k + 1] = g[30];
+        c.sZ[k * (1 + DIM)] = (Real)g[31];
+        c.sTrs[k] = (Real)g[28];
+        c.sJ[k] = (int8_t)j;
         for (int f = 0, fi = 0; f < NV; ++f) {
             if (f == j) continue;
-            for (int c = 0; c < 3; ++c) sNrm[(k * DIM + fi) * 3 + c] = (Real)g[12 + 3 * f + c];
-            sLiftc[k * DIM + fi] = (Real)(dt * g[24 + f] * g[28]);
-            sNslot[k * DIM + fi] = info[4 + f];
+            for (int q = 0; q < 3; ++q) c.sNrm[(k * DIM + fi) * 3 + q] = (Real)g[12 + 3 * f + q];
+            c.sLiftc[k * DIM + fi] = (Real)(dt * g[24 + f] * g[28]);
+            c.sNslot[k * DIM + fi] = info[4 + f];
             ++fi;
         }
     }
-    // state rows (pads zero); U buffers and facet buffers zeroed so their pads stay zero
     for (int idx = tid; idx < ns * ESZ; idx += NT) {
         const int k = idx / ESZ, r = idx - k * ESZ, s = r / NBP, b = r - s * NBP;
-        sY[idx] = b < NB ? state[((int64_t)a.patch_elem[pb + k] * NF + s) * NB + b] : Real(0);
-        sUa[idx] = Real(0);
-        sUb[idx] = Real(0);
+        c.sY[idx] = b < NB ? src[((int64_t)a.patch_elem[c.pb + k] * NF + s) * NB + b] : Real(0);
+        c.sUa[idx] = Real(0);
+        c.sUb[idx] = Real(0);
     }
-    for (int idx = tid; idx < ns * TSZ; idx += NT) sTr[idx] = Real(0);
+    for (int idx = tid; idx < ns * TSZ; idx += NT) c.sTr[idx] = Real(0);
     __syncthreads();
     // neighbour's facet position (needs the neighbour's j) and impedance
     for (int k = tid; k < ns; k += NT) {
-        const int8_t* info = a.patch_info + (pb + k) * 12;
-        const int j = sJ[k];
+        const int8_t* info = a.patch_info + (c.pb + k) * 12;
+        const int j = c.sJ[k];
         for (int f = 0, fi = 0; f < NV; ++f) {
             if (f == j) continue;
             const int s2 = info[4 + f];
             int8_t nfi = -1;
-            Real z2 = sZ[k * (1 + DIM)];
+            Real z2 = c.sZ[k * (1 + DIM)];
             if (s2 >= 0) {
                 const int f2 = info[8 + f];
-                nfi = (int8_t)(f2 - (f2 > sJ[s2] ? 1 : 0));
-                z2 = sZ[s2 * (1 + DIM)];
+                nfi = (int8_t)(f2 - (f2 > c.sJ[s2] ? 1 : 0));
+                z2 = c.sZ[s2 * (1 + DIM)];
             }
-            sNfi[k * DIM + fi] = nfi;
-            sZ[k * (1 + DIM) + 1 + fi] = z2;
+            c.sNfi[k * DIM + fi] = nfi;
+            c.sZ[k * (1 + DIM) + 1 + fi] = z2;
             ++fi;
         }
     }
     __syncthreads();
+}
 
-    Real* Ucur = sUa;
-    Real* Unext = sUb;
-    for (int i = 0; i < a.m; ++i) {
-        const double ti = (double)i / (double)a.m;
-        // G(t_i)^-1 per element, FP64 -> state precision
-        for (int k = tid; k < ns; k += NT) {
-            double g[3];
-            for (int c = 0; c < 3; ++c) g[c] = sGphi[3 * k + c] + ti * sGdel[3 * k + c];
-            const double eps = sMat[2 * k], mu = sMat[2 * k + 1];
-            if (!(g[0] * g[0] + g[1] * g[1] + g[2] * g[2] < eps * mu)) atomicExch(a.err, 1);
-            for (int s = 0; s < NF; ++s) {
-                double w[6] = {0, 0, 0, 0, 0, 0}, o[6];
-                w[field6<DIM>(s)] = 1.0;
-                ginv_apply(w, g, eps, mu, o);
-                for (int r = 0; r < NF; ++r) sGi[(k * NF + r) * NF + s] = (Real)o[field6<DIM>(r)];
-            }
+// G(t_i)^-1 per element, built in FP64 from the closed form, stored in the state precision.
+template <typename Real, int DIM, int P>
+__device__ void tent_ginv(TentCtx<Real, DIM, P>& c, const KArgs& a, int i) {
+    using Sh = Shape<DIM, P>;
+    constexpr int NF = Sh::NF, NT = Sh::NT;
+    const double ti = (double)i / (double)a.m;
+    for (int k = threadIdx.x; k < c.ns; k += NT) {
+        double g[3];
+        for (int q = 0; q < 3; ++q) g[q] = c.sGphi[3 * k + q] + ti * c.sGdel[3 * k + q];
+        const double eps = c.sMat[2 * k], mu = c.sMat[2 * k + 1];
+        if (!(g[0] * g[0] + g[1] * g[1] + g[2] * g[2] < eps * mu)) atomicExch(a.err, 1);
+        for (int s = 0; s < NF; ++s) {
+            double w[6] = {0, 0, 0, 0, 0, 0}, o[6];
+            w[field6<DIM>(s)] = 1.0;
+            ginv_apply(w, g, eps, mu, o);
+            for (int r = 0; r < NF; ++r) c.sGi[(k * NF + r) * NF + s] = (Real)o[field6<DIM>(r)];
         }
-        __syncthreads();
-        // U_{i,0} = G_i^-1 Y_{i,0}
-        for (int idx = tid; idx < ns * NB; idx += NT) {
-            const int k = idx / NB, b = idx - k * NB;
-            const Real* Gi = sGi + k * NF * NF;
-            Real y[NF];
+    }
+}
+
+// dst = G^-1 src per coefficient column (b < NB)
+template <typename Real, int DIM, int P>
+__device__ void tent_apply_ginv(TentCtx<Real, DIM, P>& c, const Real* src, Real* dst) {
+    using Sh = Shape<DIM, P>;
+    constexpr int NF = Sh::NF, NB = Sh::NB, NT = Sh::NT, ESZ = NF * Sh::NBP, NBP = Sh::NBP;
+    for (int idx = threadIdx.x; idx < c.ns * NB; idx += NT) {
+        const int k = idx / NB, b = idx - k * NB;
+        const Real* Gi = c.sGi + k * NF * NF;
+        Real y[NF];
 #pragma unroll
-            for (int s = 0; s < NF; ++s) y[s] = sY[k * ESZ + s * NBP + b];
+        for (int s = 0; s < NF; ++s) y[s] = src[k * ESZ + s * NBP + b];
 #pragma unroll
-            for (int r = 0; r < NF; ++r) {
-                Real acc = 0;
+        for (int r = 0; r < NF; ++r) {
+            Real acc = 0;
 #pragma unroll
-                for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * y[s];
-                Ucur[k * ESZ + r * NBP + b] = acc;
-            }
+            for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * y[s];
+            dst[k * ESZ + r * NBP + b] = acc;
         }
-        __syncthreads();
-        for (int n = 1; n <= a.q; ++n) {
-            // ---- (b1) facet traces of U on the facets containing V (two modes per thread) ----
-            for (int idx = tid; idx < ns * DIM * NCG; idx += NT) {
-                const int k = idx / (DIM * NCG), rem = idx - k * DIM * NCG, fi = rem / NCG;
-                const int c0 = (rem - fi * NCG) * AP;
-                const int j = sJ[k];
-                const int f = fi + (fi >= j ? 1 : 0);
-                const Real* U = Ucur + k * ESZ;
-                const Real* T0 = Tr + ((size_t)f * NFB + c0) * NBP;
-                const bool two = c0 + 1 < NFB;
-                const Real* T1 = two ? T0 + NBP : T0;
-                Real acc[AP][NF];
+    }
+}
+
+// (b1) facet traces of U on the facets containing V, two modes per thread, into tr
+template <typename Real, int DIM, int P>
+__device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real* Ucur, Real* tr) {
+    using Sh = Shape<DIM, P>;
+    using VT = typename Vec<Real>::T;
+    constexpr int NF = Sh::NF, NFB = Sh::NFB, NT = Sh::NT, NBP = Sh::NBP, NFBP = Sh::NFBP;
+    constexpr int AP = Sh::AP, NCG = Sh::NCG, W = Vec<Real>::W, ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
+    const Real* Tr = (const Real*)a.Tr;
+    for (int idx = threadIdx.x; idx < c.ns * DIM * NCG; idx += NT) {
+        const int k = idx / (DIM * NCG), rem = idx - k * DIM * NCG, fi = rem / NCG;
+        const int c0 = (rem - fi * NCG) * AP;
+        const int j = c.sJ[k];
+        const int f = fi + (fi >= j ? 1 : 0);
+        const Real* U = Ucur + k * ESZ;
+        const Real* T0 = Tr + ((size_t)f * NFB + c0) * NBP;
+        const bool two = c0 + 1 < NFB;
+        const Real* T1 = two ? T0 + NBP : T0;
+        Real acc[AP][NF];
 #pragma unroll
-                for (int ci = 0; ci < AP; ++ci)
+        for (int ci = 0; ci < AP; ++ci)
 #pragma unroll
-                    for (int s = 0; s < NF; ++s) acc[ci][s] = 0;
+            for (int s = 0; s < NF; ++s) acc[ci][s] = 0;
 #pragma unroll 1
-                for (int b = 0; b < NBP; b += W) {
-                    Real t0v[W], t1v[W];
-                    Vec<Real>::get(__ldg((const VT*)(T0 + b)), t0v);
-                    Vec<Real>::get(__ldg((const VT*)(T1 + b)), t1v);
+        for (int b = 0; b < NBP; b += W) {
+            Real t0v[W], t1v[W];
+            Vec<Real>::get(__ldg((const VT*)(T0 + b)), t0v);
+            Vec<Real>::get(__ldg((const VT*)(T1 + b)), t1v);
 #pragma unroll
-                    for (int s = 0; s < NF; ++s) {
-                        Real u[W];
-                        Vec<Real>::get(*(const VT*)(U + s * NBP + b), u);
+            for (int s = 0; s < NF; ++s) {
+                Real u[W];
+                Vec<Real>::get(*(const VT*)(U + s * NBP + b), u);
 #pragma unroll
-                        for (int v = 0; v < W; ++v) {
-                            acc[0][s] += t0v[v] * u[v];
-                            acc[1][s] += t1v[v] * u[v];
-                        }
-                    }
+                for (int v = 0; v < W; ++v) {
+                    acc[0][s] += t0v[v] * u[v];
+                    acc[1][s] += t1v[v] * u[v];
                 }
-                const Real sc = sTrs[k];
-                Real* out = sTr + k * TSZ + fi * NF * NFBP + c0;
+            }
+        }
+        const Real sc = c.sTrs[k];
+        Real* out = tr + k * TSZ + fi * NF * NFBP + c0;
+#pragma unroll
+        for (int s = 0; s < NF; ++s) {
+            out[s * NFBP] = acc[0][s] * sc;
+            if (two) out[s * NFBP + 1] = acc[1][s] * sc;
+        }
+    }
+}
+
+// (b2) numerical flux, once per facet (lower slot owns an interior facet), in place in tr,
+// pre-scaled by each side's lift factor dt (d-1)!|F| / sqrt|det J|
+template <typename Real, int DIM, int P>
+__device__ void tent_fluxes(TentCtx<Real, DIM, P>& c, Real* tr) {
+    using Sh = Shape<DIM, P>;
+    constexpr int NF = Sh::NF, NFB = Sh::NFB, NT = Sh::NT, NFBP = Sh::NFBP, TSZ = DIM * NF * NFBP;
+    for (int idx = threadIdx.x; idx < c.ns * DIM * NFB; idx += NT) {
+        const int k = idx / (DIM * NFB), rem = idx - k * DIM * NFB, fi = rem / NFB, cc = rem - fi * NFB;
+        const int s2 = c.sNslot[k * DIM + fi];
+        if (s2 >= 0 && s2 < k) continue;
+        Real* mine = tr + k * TSZ + fi * NF * NFBP + cc;
+        Real um[6] = {0, 0, 0, 0, 0, 0}, up[6] = {0, 0, 0, 0, 0, 0}, F[6], nrm[3];
+#pragma unroll
+        for (int s = 0; s < NF; ++s) um[field6<DIM>(s)] = mine[s * NFBP];
+        Real* other = nullptr;
+        if (s2 >= 0) {
+            other = tr + s2 * TSZ + c.sNfi[k * DIM + fi] * NF * NFBP + cc;
+#pragma unroll
+            for (int s = 0; s < NF; ++s) up[field6<DIM>(s)] = other[s * NFBP];
+        } else {
+#pragma unroll
+            for (int s = 0; s < 6; ++s) up[s] = s < 3 ? -um[s] : um[s];
+        }
+        for (int q = 0; q < 3; ++q) nrm[q] = c.sNrm[(k * DIM + fi) * 3 + q];
+        upwind6<Real>(um, up, nrm, c.sZ[k * (1 + DIM)], c.sZ[k * (1 + DIM) + 1 + fi], F);
+        const Real lc = c.sLiftc[k * DIM + fi];
+#pragma unroll
+        for (int s = 0; s < NF; ++s) mine[s * NFBP] = lc * F[field6<DIM>(s)];
+        if (other) {
+            const Real lc2 = c.sLiftc[s2 * DIM + c.sNfi[k * DIM + fi]];
+#pragma unroll
+            for (int s = 0; s < NF; ++s) other[s * NFBP] = -lc2 * F[field6<DIM>(s)];
+        }
+    }
+}
+
+// (b3)+(c) Y_{i,n} = A U_{i,n-1} (volume + lift of the scaled fluxes in tr), Taylor
+// accumulation into sY, and U_{i,n} = G_i^-1 (Y_{i,n} - n M' U_{i,n-1}) into Unext (n < q)
+template <typename Real, int DIM, int P>
+__device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, const Real* Ucur, Real* Unext,
+                           const Real* tr) {
+    using Sh = Shape<DIM, P>;
+    using VT = typename Vec<Real>::T;
+    constexpr int NF = Sh::NF, NB = Sh::NB, NV = Sh::NV, NT = Sh::NT, NBP = Sh::NBP, NFBP = Sh::NFBP;
+    constexpr int AP = Sh::AP, NAG = Sh::NAG, W = Vec<Real>::W, ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
+    const Real* S = (const Real*)a.S;
+    const Real* Lf = (const Real*)a.L;
+    const Real cn = (Real)a.taylor[n];
+    const Real nn = (Real)n;
+    for (int idx = threadIdx.x; idx < c.ns * NAG; idx += NT) {
+        const int k = idx / NAG, a0 = (idx - k * NAG) * AP;
+        const bool two = a0 + 1 < NB;
+        const int j = c.sJ[k];
+        const Real* U = Ucur + k * ESZ;
+        Real Pm[AP][DIM][NF];
+#pragma unroll
+        for (int ai = 0; ai < AP; ++ai)
+#pragma unroll
+            for (int l = 0; l < DIM; ++l)
+#pragma unroll
+                for (int s = 0; s < NF; ++s) Pm[ai][l][s] = 0;
+        const Real* S0 = S + ((size_t)j * DIM * NB + a0) * NBP;
+        const Real* S1 = two ? S0 + NBP : S0;
+#pragma unroll 1
+        for (int b = 0; b < NBP; b += W) {
+            Real sv[AP][DIM][W];
+#pragma unroll
+            for (int l = 0; l < DIM; ++l) {
+                Vec<Real>::get(__ldg((const VT*)(S0 + (size_t)l * NB * NBP + b)), sv[0][l]);
+                Vec<Real>::get(__ldg((const VT*)(S1 + (size_t)l * NB * NBP + b)), sv[1][l]);
+            }
+#pragma unroll
+            for (int s = 0; s < NF; ++s) {
+                Real u[W];
+                Vec<Real>::get(*(const VT*)(U + s * NBP + b), u);
+#pragma unroll
+                for (int v = 0; v < W; ++v)
+#pragma unroll
+                    for (int ai = 0; ai < AP; ++ai)
+#pragma unroll
+                        for (int l = 0; l < DIM; ++l) Pm[ai][l][s] += sv[ai][l][v] * u[v];
+            }
+        }
+        Real Yn[AP][NF];
+        const Real* ac = c.sAc + k * DIM * 3;
+#pragma unroll
+        for (int ai = 0; ai < AP; ++ai) {
+            if constexpr (DIM == 3) {
+                Real vE[3] = {0, 0, 0}, vH[3] = {0, 0, 0};
+#pragma unroll
+                for (int l = 0; l < DIM; ++l) {
+                    const Real ax = ac[3 * l], ay = ac[3 * l + 1], az = ac[3 * l + 2];
+                    const Real* Pl = Pm[ai][l];
+                    vE[0] -= ay * Pl[5] - az * Pl[4];   // -a x P_H
+                    vE[1] -= az * Pl[3] - ax * Pl[5];
+                    vE[2] -= ax * Pl[4] - ay * Pl[3];
+                    vH[0] += ay * Pl[2] - az * Pl[1];   //  a x P_E
+                    vH[1] += az * Pl[0] - ax * Pl[2];
+                    vH[2] += ax * Pl[1] - ay * Pl[0];
+                }
+#pragma unroll
+                for (int q = 0; q < 3; ++q) { Yn[ai][q] = vE[q]; Yn[ai][3 + q] = vH[q]; }
+            } else {
+                Real ex = 0, ey = 0, hz = 0;
+#pragma unroll
+                for (int l = 0; l < DIM; ++l) {
+                    const Real ax = ac[3 * l], ay = ac[3 * l + 1];
+                    const Real* Pl = Pm[ai][l];
+                    ex -= ay * Pl[2];
+                    ey += ax * Pl[2];
+                    hz += ax * Pl[1] - ay * Pl[0];
+                }
+                Yn[ai][0] = ex; Yn[ai][1] = ey; Yn[ai][2] = hz;
+            }
+        }
+        // lift of the (already scaled) facet fluxes
+#pragma unroll
+        for (int fi = 0; fi < DIM; ++fi) {
+            const int f = fi + (fi >= j ? 1 : 0);
+            const Real* L0 = Lf + (((size_t)j * NV + f) * NB + a0) * NFBP;
+            const Real* L1 = two ? L0 + NFBP : L0;
+            const Real* Fx = tr + k * TSZ + fi * NF * NFBP;
+            Real acc[AP][NF];
+#pragma unroll
+            for (int ai = 0; ai < AP; ++ai)
+#pragma unroll
+                for (int s = 0; s < NF; ++s) acc[ai][s] = 0;
+#pragma unroll
+            for (int cc = 0; cc < NFBP; cc += W) {
+                Real l0[W], l1[W];
+                Vec<Real>::get(__ldg((const VT*)(L0 + cc)), l0);
+                Vec<Real>::get(__ldg((const VT*)(L1 + cc)), l1);
 #pragma unroll
                 for (int s = 0; s < NF; ++s) {
-                    out[s * NFBP] = acc[0][s] * sc;
-                    if (two) out[s * NFBP + 1] = acc[1][s] * sc;
+                    Real fv[W];
+                    Vec<Real>::get(*(const VT*)(Fx + s * NFBP + cc), fv);
+#pragma unroll
+                    for (int v = 0; v < W; ++v) {
+                        acc[0][s] += l0[v] * fv[v];
+                        acc[1][s] += l1[v] * fv[v];
+                    }
                 }
             }
-            __syncthreads();
-            // ---- (b2) numerical flux, once per facet (lower slot owns an interior facet) ----
-            for (int idx = tid; idx < ns * DIM * NFB; idx += NT) {
-                const int k = idx / (DIM * NFB), rem = idx - k * DIM * NFB, fi = rem / NFB, c = rem - fi * NFB;
-                const int s2 = sNslot[k * DIM + fi];
-                if (s2 >= 0 && s2 < k) continue;
-                Real* mine = sTr + k * TSZ + fi * NF * NFBP + c;
-                Real um[6] = {0, 0, 0, 0, 0, 0}, up[6] = {0, 0, 0, 0, 0, 0}, F[6], nrm[3];
 #pragma unroll
-                for (int s = 0; s < NF; ++s) um[field6<DIM>(s)] = mine[s * NFBP];
-                Real* other = nullptr;
-                if (s2 >= 0) {
-                    other = sTr + s2 * TSZ + sNfi[k * DIM + fi] * NF * NFBP + c;
+            for (int ai = 0; ai < AP; ++ai)
 #pragma unroll
-                    for (int s = 0; s < NF; ++s) up[field6<DIM>(s)] = other[s * NFBP];
+                for (int s = 0; s < NF; ++s) Yn[ai][s] -= acc[ai][s];
+        }
+        const Real* gd = c.sGd + 3 * k;
+        const Real* Gi = c.sGi + k * NF * NF;
+#pragma unroll
+        for (int ai = 0; ai < AP; ++ai) {
+            if (ai == 1 && !two) break;
+            const int av = a0 + ai;
+#pragma unroll
+            for (int s = 0; s < NF; ++s) c.sY[k * ESZ + s * NBP + av] += cn * Yn[ai][s];
+            if (n < a.q) {
+                Real r6[NF];
+                if constexpr (DIM == 3) {
+                    const Real E0 = U[0 * NBP + av], E1 = U[1 * NBP + av], E2 = U[2 * NBP + av];
+                    const Real H0 = U[3 * NBP + av], H1 = U[4 * NBP + av], H2 = U[5 * NBP + av];
+                    // M'U = [-H x gd ; E x gd]
+                    r6[0] = Yn[ai][0] + nn * (H1 * gd[2] - H2 * gd[1]);
+                    r6[1] = Yn[ai][1] + nn * (H2 * gd[0] - H0 * gd[2]);
+                    r6[2] = Yn[ai][2] + nn * (H0 * gd[1] - H1 * gd[0]);
+                    r6[3] = Yn[ai][3] - nn * (E1 * gd[2] - E2 * gd[1]);
+                    r6[4] = Yn[ai][4] - nn * (E2 * gd[0] - E0 * gd[2]);
+                    r6[5] = Yn[ai][5] - nn * (E0 * gd[1] - E1 * gd[0]);
                 } else {
-#pragma unroll
-                    for (int s = 0; s < 6; ++s) up[s] = s < 3 ? -um[s] : um[s];
+                    const Real Ex = U[0 * NBP + av], Ey = U[1 * NBP + av], Hz = U[2 * NBP + av];
+                    // M'U (TE) = (Hz gy, -Hz gx, Ex gy - Ey gx)
+                    r6[0] = Yn[ai][0] - nn * (Hz * gd[1]);
+                    r6[1] = Yn[ai][1] + nn * (Hz * gd[0]);
+                    r6[2] = Yn[ai][2] - nn * (Ex * gd[1] - Ey * gd[0]);
                 }
-                for (int cc = 0; cc < 3; ++cc) nrm[cc] = sNrm[(k * DIM + fi) * 3 + cc];
-                upwind6<Real>(um, up, nrm, sZ[k * (1 + DIM)], sZ[k * (1 + DIM) + 1 + fi], F);
-                const Real lc = sLiftc[k * DIM + fi];
 #pragma unroll
-                for (int s = 0; s < NF; ++s) mine[s * NFBP] = lc * F[field6<DIM>(s)];
-                if (other) {
-                    const Real lc2 = sLiftc[s2 * DIM + sNfi[k * DIM + fi]];
+                for (int r = 0; r < NF; ++r) {
+                    Real acc = 0;
 #pragma unroll
-                    for (int s = 0; s < NF; ++s) other[s * NFBP] = -lc2 * F[field6<DIM>(s)];
+                    for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * r6[s];
+                    Unext[k * ESZ + r * NBP + av] = acc;
                 }
             }
+        }
+    }
+}
+
+// copy ns x ESZ coefficients between shared memory and a tape slot in global memory
+template <typename Real, int DIM, int P>
+__device__ void tent_copy(int ns, const Real* src, Real* dst) {
+    constexpr int ESZ = Shape<DIM, P>::NF * Shape<DIM, P>::NBP;
+    for (int idx = threadIdx.x; idx < ns * ESZ; idx += Shape<DIM, P>::NT) dst[idx] = src[idx];
+}
+
+// All m x q SAT stages of one tent on the shared-memory state sY.  With a tape, Y_{i,0}
+// goes to slot i and U_{i,n} to slot m + i q + n (each slot max_patch x ESZ entries).
+template <typename Real, int DIM, int P>
+__device__ void tent_sat(TentCtx<Real, DIM, P>& c, const KArgs& a, Real* tape) {
+    constexpr int ESZ = Shape<DIM, P>::NF * Shape<DIM, P>::NBP;
+    const size_t slot = (size_t)a.max_patch * ESZ;
+    for (int i = 0; i < a.m; ++i) {
+        tent_ginv(c, a, i);
+        if (tape) tent_copy<Real, DIM, P>(c.ns, c.sY, tape + (size_t)i * slot);
+        __syncthreads();
+        Real* Ucur = c.sUa;
+        Real* Unext = c.sUb;
+        tent_apply_ginv(c, c.sY, Ucur);
+        __syncthreads();
+        for (int n = 1; n <= a.q; ++n) {
+            if (tape) tent_copy<Real, DIM, P>(c.ns, Ucur, tape + (size_t)(a.m + i * a.q + n - 1) * slot);
+            tent_traces(c, a, Ucur, c.sTr);
             __syncthreads();
-            // ---- (b3)+(c) volume + lift, Taylor accumulation, next U (two basis functions) ----
-            const Real cn = (Real)a.taylor[n];
-            const Real nn = (Real)n;
-            for (int idx = tid; idx < ns * NAG; idx += NT) {
-                const int k = idx / NAG, a0 = (idx - k * NAG) * AP;
-                const bool two = a0 + 1 < NB;
-                const int j = sJ[k];
-                const Real* U = Ucur + k * ESZ;
-                Real Pm[AP][DIM][NF];
-#pragma unroll
-                for (int ai = 0; ai < AP; ++ai)
-#pragma unroll
-                    for (int l = 0; l < DIM; ++l)
-#pragma unroll
-                        for (int s = 0; s < NF; ++s) Pm[ai][l][s] = 0;
-                const Real* S0 = S + ((size_t)j * DIM * NB + a0) * NBP;
-                const Real* S1 = two ? S0 + NBP : S0;
-#pragma unroll 1
-                for (int b = 0; b < NBP; b += W) {
-                    Real sv[AP][DIM][W];
-#pragma unroll
-                    for (int l = 0; l < DIM; ++l) {
-                        Vec<Real>::get(__ldg((const VT*)(S0 + (size_t)l * NB * NBP + b)), sv[0][l]);
-                        Vec<Real>::get(__ldg((const VT*)(S1 + (size_t)l * NB * NBP + b)), sv[1][l]);
-                    }
-#pragma unroll
-                    for (int s = 0; s < NF; ++s) {
-                        Real u[W];
-                        Vec<Real>::get(*(const VT*)(U + s * NBP + b), u);
-#pragma unroll
-                        for (int v = 0; v < W; ++v)
-#pragma unroll
-                            for (int ai = 0; ai < AP; ++ai)
-#pragma unroll
-                                for (int l = 0; l < DIM; ++l) Pm[ai][l][s] += sv[ai][l][v] * u[v];
-                    }
-                }
-                Real Yn[AP][NF];
-                const Real* ac = sAc + k * DIM * 3;
-#pragma unroll
-                for (int ai = 0; ai < AP; ++ai) {
-                    if constexpr (DIM == 3) {
-                        Real vE[3] = {0, 0, 0}, vH[3] = {0, 0, 0};
-#pragma unroll
-                        for (int l = 0; l < DIM; ++l) {
-                            const Real ax = ac[3 * l], ay = ac[3 * l + 1], az = ac[3 * l + 2];
-                            const Real* Pl = Pm[ai][l];
-                            vE[0] -= ay * Pl[5] - az * Pl[4];   // -a x P_H
-                            vE[1] -= az * Pl[3] - ax * Pl[5];
-                            vE[2] -= ax * Pl[4] - ay * Pl[3];
-                            vH[0] += ay * Pl[2] - az * Pl[1];   //  a x P_E
-                            vH[1] += az * Pl[0] - ax * Pl[2];
-                            vH[2] += ax * Pl[1] - ay * Pl[0];
-                        }
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) { Yn[ai][c] = vE[c]; Yn[ai][3 + c] = vH[c]; }
-                    } else {
-                        Real ex = 0, ey = 0, hz = 0;
-#pragma unroll
-                        for (int l = 0; l < DIM; ++l) {
-                            const Real ax = ac[3 * l], ay = ac[3 * l + 1];
-                            const Real* Pl = Pm[ai][l];
-                            ex -= ay * Pl[2];
-                            ey += ax * Pl[2];
-                            hz += ax * Pl[1] - ay * Pl[0];
-                        }
-                        Yn[ai][0] = ex; Yn[ai][1] = ey; Yn[ai][2] = hz;
-                    }
-                }
-                // lift of the (already dt (d-1)!|F|/sqrt|det J|-scaled) facet fluxes
-#pragma unroll
-                for (int fi = 0; fi < DIM; ++fi) {
-                    const int f = fi + (fi >= j ? 1 : 0);
-                    const Real* L0 = Lf + (((size_t)j * NV + f) * NB + a0) * NFBP;
-                    const Real* L1 = two ? L0 + NFBP : L0;
-                    const Real* Fx = sTr + k * TSZ + fi * NF * NFBP;
-                    Real acc[AP][NF];
-#pragma unroll
-                    for (int ai = 0; ai < AP; ++ai)
-#pragma unroll
-                        for (int s = 0; s < NF; ++s) acc[ai][s] = 0;
-#pragma unroll
-                    for (int c = 0; c < NFBP; c += W) {
-                        Real l0[W], l1[W];
-                        Vec<Real>::get(__ldg((const VT*)(L0 + c)), l0);
-                        Vec<Real>::get(__ldg((const VT*)(L1 + c)), l1);
-#pragma unroll
-                        for (int s = 0; s < NF; ++s) {
-                            Real fv[W];
-                            Vec<Real>::get(*(const VT*)(Fx + s * NFBP + c), fv);
-#pragma unroll
-                            for (int v = 0; v < W; ++v) {
-                                acc[0][s] += l0[v] * fv[v];
-                                acc[1][s] += l1[v] * fv[v];
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int ai = 0; ai < AP; ++ai)
-#pragma unroll
-                        for (int s = 0; s < NF; ++s) Yn[ai][s] -= acc[ai][s];
-                }
-                const Real* gd = sGd + 3 * k;
-                const Real* Gi = sGi + k * NF * NF;
-#pragma unroll
-                for (int ai = 0; ai < AP; ++ai) {
-                    if (ai == 1 && !two) break;
-                    const int av = a0 + ai;
-                    // Taylor accumulation Y_{i+1,0} += (1/m)^n/n! Y_{i,n}
-#pragma unroll
-                    for (int s = 0; s < NF; ++s) sY[k * ESZ + s * NBP + av] += cn * Yn[ai][s];
-                    if (n < a.q) {
-                        // U_{i,n} = G_i^-1 (Y_{i,n} - n M' U_{i,n-1})
-                        Real r6[NF];
-                        if constexpr (DIM == 3) {
-                            const Real E0 = U[0 * NBP + av], E1 = U[1 * NBP + av], E2 = U[2 * NBP + av];
-                            const Real H0 = U[3 * NBP + av], H1 = U[4 * NBP + av], H2 = U[5 * NBP + av];
-                            // M'U = [-H x gd ; E x gd]
-                            r6[0] = Yn[ai][0] + nn * (H1 * gd[2] - H2 * gd[1]);
-                            r6[1] = Yn[ai][1] + nn * (H2 * gd[0] - H0 * gd[2]);
-                            r6[2] = Yn[ai][2] + nn * (H0 * gd[1] - H1 * gd[0]);
-                            r6[3] = Yn[ai][3] - nn * (E1 * gd[2] - E2 * gd[1]);
-                            r6[4] = Yn[ai][4] - nn * (E2 * gd[0] - E0 * gd[2]);
-                            r6[5] = Yn[ai][5] - nn * (E0 * gd[1] - E1 * gd[0]);
-                        } else {
-                            const Real Ex = U[0 * NBP + av], Ey = U[1 * NBP + av], Hz = U[2 * NBP + av];
-                            // M'U (TE) = (Hz gy, -Hz gx, Ex gy - Ey gx)
-                            r6[0] = Yn[ai][0] - nn * (Hz * gd[1]);
-                            r6[1] = Yn[ai][1] + nn * (Hz * gd[0]);
-                            r6[2] = Yn[ai][2] - nn * (Ex * gd[1] - Ey * gd[0]);
-                        }
-#pragma unroll
-                        for (int r = 0; r < NF; ++r) {
-                            Real acc = 0;
-#pragma unroll
-                            for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * r6[s];
-                            Unext[k * ESZ + r * NBP + av] = acc;
-                        }
-                    }
-                }
-            }
+            tent_fluxes(c, c.sTr);
+            __syncthreads();
+            tent_stage(c, a, n, Ucur, Unext, c.sTr);
             __syncthreads();
             Real* tmp = Ucur; Ucur = Unext; Unext = tmp;
         }
     }
+}
+
+template <typename Real, int DIM, int P>
+__global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_layer_kernel(const KArgs a, int64_t t0) {
+    using Sh = Shape<DIM, P>;
+    constexpr int NF = Sh::NF, NB = Sh::NB, NT = Sh::NT, NBP = Sh::NBP, ESZ = NF * NBP;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const SmemLayout<Real, DIM, P> lay(a.max_patch);
+    TentCtx<Real, DIM, P> c;
+    c.carve(smem, lay);
+    const int64_t tent = t0 + blockIdx.x;
+    Real* state = (Real*)a.state + (int64_t)blockIdx.y * a.rhs_stride;
+    tent_setup(c, a, tent, state);
+    tent_sat(c, a, (Real*)nullptr);
     // ---- (d) scatter the tent-top Y; advance the front at V ----
     bool bad = false;
-    for (int idx = tid; idx < ns * NF * NB; idx += NT) {
+    for (int idx = threadIdx.x; idx < c.ns * NF * NB; idx += NT) {
         const int k = idx / (NF * NB), r = idx - k * NF * NB, s = r / NB, b = r - s * NB;
-        const Real v = sY[k * ESZ + s * NBP + b];
+        const Real v = c.sY[k * ESZ + s * NBP + b];
         if (!isfinite((double)v)) bad = true;
-        state[(int64_t)a.patch_elem[pb + k] * NF * NB + r] = v;
+        state[(int64_t)a.patch_elem[c.pb + k] * NF * NB + r] = v;
     }
     if (bad) atomicExch(a.err, 2);
-    if (tid == 0 && blockIdx.y == 0) a.tau[V] = a.tent_tt[tent];
+    if (threadIdx.x == 0 && blockIdx.y == 0) a.tau[c.V] = a.tent_tt[tent];
 }
 
 }  // namespace mtp

@@ -34,6 +34,17 @@ struct KernelEntry {
 void kernel_table_f64(KernelEntry entries[2][4]);
 void kernel_table_f32(KernelEntry entries[2][4]);
 
+struct AdjArgs;
+using AdjLaunchFn = cudaError_t (*)(const AdjArgs&, int64_t t0, int n_tents, int n_rhs, cudaStream_t st);
+using TapeStrideFn = int64_t (*)(int max_patch, int m, int q);
+struct AdjEntry {
+    AdjLaunchFn launch;
+    PrepareFn prepare;
+    TapeStrideFn tape_stride;
+};
+// entries[precision][dim - 2][p - 1]
+void adjoint_table(AdjEntry entries[2][2][4]);
+
 #define MTP_KERNEL_TABLE(NAME, REAL)                                                   \
     void NAME(KernelEntry e[2][4]) {                                                   \
         e[0][0] = {launch_tent_kernel<REAL, 2, 1>, prepare_tent_kernel<REAL, 2, 1>};   \
