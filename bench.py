@@ -36,7 +36,7 @@ N_SMS = 152
 # DRAM bytes (read + write) per tent of the FP32 p=4 tent kernel from the last ncu capture of
 # the current kernel version (profiles/tent_layer_kernel_fp32_p4_graded32.md); None once the
 # kernel has changed since the counters were taken.
-TRAFFIC_BYTES_PER_TENT = {"fp32": 27452.0}
+TRAFFIC_BYTES_PER_TENT = {}
 
 
 def load_peaks():
@@ -224,13 +224,15 @@ def run_mtp(args):
     w = make_workload(args.workload)
     prec = mtp.MTP_FP32 if args.precision == "fp32" else mtp.MTP_FP64
     t0 = time.perf_counter()
-    mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=prec)
+    flags = mtp.MTP_FLAG_LAYER_LAUNCHES if args.layer_launches else 0
+    mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=prec, flags=flags)
     t1 = time.perf_counter()
     tents = mesh.pitch(w.T, w.causality)
     t2 = time.perf_counter()
     tl = tents.get()
     n_layers = tents.info["n_layers"]
-    launches_per_step = int(np.count_nonzero(np.diff(tl["layer_ptr"])))
+    persistent = not args.layer_launches
+    launches_per_step = 1 if persistent else int(np.count_nonzero(np.diff(tl["layer_ptr"])))
     dofs = tents.info["spacetime_dofs"]
     vals0 = torch.tensor(initial_lattice(w)[None], device="cuda")
     state0 = mesh.state_from_lattice(vals0)
@@ -282,7 +284,8 @@ def run_mtp(args):
     traffic = None if tpl is None else tpl * tents.info["n_tents"] / launches_per_step
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": f"tent_layer_kernel<{args.precision},3,{w.p}>",
+                "kernel": (f"tent_persistent_kernel<{args.precision},3,{w.p}>" if persistent
+                           else f"tent_layer_kernel<{args.precision},3,{w.p}>"),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)"}
 
     # end to end through the host-buffer entry point (pinned buffers, copies in the timed region)
@@ -368,6 +371,7 @@ def main():
     ap.add_argument("--workload", default="graded", choices=["graded", "cube", "small"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--fp64-window", type=float, default=0.02)
+    ap.add_argument("--layer-launches", action="store_true", help="one launch per layer instead of the DAG walk")
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
     ap.add_argument("--cpu-tents", type=int, default=80)
     ap.add_argument("--cpu-rounds", type=int, default=80)

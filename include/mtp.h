@@ -49,6 +49,10 @@ extern "C" {
 #define MTP_ENUMERIC     -7   /* NaN / Inf detected */
 #define MTP_EUNSUPPORTED -8   /* combination not built (e.g. degree > 4, patch too large) */
 
+/* mtp_options.flags bits */
+#define MTP_FLAG_LAYER_LAUNCHES 1   /* mtp_evolve: one launch per layer (CUDA graph) instead of the
+                                       persistent DAG-walking kernel */
+
 /* precision of the state and of the operator arithmetic */
 #define MTP_FP64 0
 #define MTP_FP32 1
@@ -62,7 +66,7 @@ typedef struct {
     int m;          /* SAT sub-intervals per tent; 0 selects 2p (Sec. 5.1)                 */
     int precision;  /* MTP_FP64 or MTP_FP32                                                */
     int n_rhs;      /* independent states evolved with the same tents (>= 1; 0 means 1)   */
-    int flags;      /* reserved, must be 0                                                 */
+    int flags;      /* MTP_FLAG_* bits; 0 by default                                       */
 } mtp_options;
 
 /* Spatial mesh and materials (Sec. 2: conforming mesh of elements T and vertices V;
@@ -119,8 +123,11 @@ int mtp_state_to_lattice(mtp_mesh_t mesh, const void* state_dev, double* vals_de
 /* Evolve the state in place from the flat front t = 0 to the flat front t = T through
  * every tent, layer by layer (Sec. 2 and 3), each tent advanced bottom to top with
  * q-stage SAT over m sub-intervals (Sec. 4, eqs. coeff_rec and recursion-init), with
- * the mass solve in the closed form of Sec. 4.  All tents of a layer (times n_rhs)
- * run in one kernel launch; the layers are replayed from a CUDA graph.  T must equal
+ * the mass solve in the closed form of Sec. 4.  Default: one persistent kernel walks the
+ * tent DAG (tents taken in layer order; a tent starts once the earlier-layer tents of its
+ * vertex and of its neighbours are done, tracked by per-vertex counters; every wait is
+ * bounded and reports MTP_ETIMEOUT); with MTP_FLAG_LAYER_LAUNCHES all tents of a layer
+ * (times n_rhs) run in one launch and the layers are replayed from a CUDA graph.  T must equal
  * the pitched T (MTP_EINVAL otherwise).  Returns after the work has completed on the
  * stream: the device-side error word is read back (MTP_ECAUSAL if a tent violated
  * causality, MTP_ENUMERIC on a non-finite result). */

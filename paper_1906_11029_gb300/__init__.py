@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libmtp.so")
 MTP_OK, MTP_EINVAL, MTP_EMESH, MTP_ECAUSAL = 0, -1, -2, -3
 MTP_ENOMEM, MTP_ECUDA, MTP_ETIMEOUT, MTP_ENUMERIC, MTP_EUNSUPPORTED = -4, -5, -6, -7, -8
 MTP_FP64, MTP_FP32 = 0, 1
+MTP_FLAG_LAYER_LAUNCHES = 1
 _CODES = {0: "MTP_OK", -1: "MTP_EINVAL", -2: "MTP_EMESH", -3: "MTP_ECAUSAL", -4: "MTP_ENOMEM",
           -5: "MTP_ECUDA", -6: "MTP_ETIMEOUT", -7: "MTP_ENUMERIC", -8: "MTP_EUNSUPPORTED"}
 
@@ -104,12 +105,12 @@ def library_path():
 
 
 # ------------------------------------------------------------------------ raw ABI names
-def mtp_mesh_create(dim, vertices, elements, eps, mu, p, precision=MTP_FP64, n_rhs=1, q=0, m=0):
+def mtp_mesh_create(dim, vertices, elements, eps, mu, p, precision=MTP_FP64, n_rhs=1, q=0, m=0, flags=0):
     v = np.ascontiguousarray(vertices, np.float64)
     e = np.ascontiguousarray(elements, np.int32)
     ep = np.ascontiguousarray(eps, np.float64)
     mu_ = np.ascontiguousarray(mu, np.float64)
-    opts = mtp_options(p, q, m, precision, n_rhs, 0)
+    opts = mtp_options(p, q, m, precision, n_rhs, flags)
     h = C.c_void_p()
     _check(_lib.mtp_mesh_create(dim, len(v), _ptr(v), len(e), _ptr(e), _ptr(ep), _ptr(mu_),
                                 C.byref(opts), C.byref(h)))
@@ -198,8 +199,8 @@ def mtp_energy_noalloc(state_dev, eps_dev, mu_dev, dim, n_elems, p, precision, n
 class Mesh:
     """Owns an mtp_mesh_t.  Arrays are host (numpy) data; see include/mtp.h."""
 
-    def __init__(self, dim, vertices, elements, eps, mu, p, precision=MTP_FP64, n_rhs=1, q=0, m=0):
-        self.h = mtp_mesh_create(dim, vertices, elements, eps, mu, p, precision, n_rhs, q, m)
+    def __init__(self, dim, vertices, elements, eps, mu, p, precision=MTP_FP64, n_rhs=1, q=0, m=0, flags=0):
+        self.h = mtp_mesh_create(dim, vertices, elements, eps, mu, p, precision, n_rhs, q, m, flags)
         self.info = mtp_mesh_info(self.h)
         self.p, self.precision, self.n_rhs = p, precision, n_rhs
         self.q = q or p + 1

@@ -47,6 +47,14 @@ struct DeviceTents {
     cudaStream_t capture = nullptr;
     cudaGraphExec_t exec = nullptr;
     void* graph_state = nullptr;  // state pointer baked into the graph
+    // persistent DAG walk
+    int32_t* tent_layer = nullptr;
+    int64_t* vt_ptr = nullptr;
+    int32_t* vt_layer = nullptr;
+    int64_t* adj_ptr = nullptr;
+    int32_t* adj = nullptr;
+    int* cnt = nullptr;
+    unsigned long long* next = nullptr;
     // adjoint work buffers (grown on demand)
     void* adj_buf = nullptr;
     size_t adj_bytes = 0;
@@ -126,7 +134,8 @@ void device_tents_free(Tents& t) {
     DeviceTents& d = *t.dev;
     if (d.exec) cudaGraphExecDestroy(d.exec);
     if (d.capture) cudaStreamDestroy(d.capture);
-    void* ptrs[] = {d.v, d.tb, d.tt, d.tau, d.err, d.host_state, d.adj_buf, d.tau_rev};
+    void* ptrs[] = {d.v, d.tb, d.tt, d.tau, d.err, d.host_state, d.adj_buf, d.tau_rev, d.tent_layer, d.vt_ptr,
+                    d.vt_layer, d.adj_ptr, d.adj, d.cnt, d.next};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (d.err_host) cudaFreeHost(d.err_host);
@@ -146,6 +155,23 @@ static int device_tents_upload(Tents& t) {
     CUDA_TRY(cudaMalloc((void**)&d.err, sizeof(int)));
     CUDA_TRY(cudaMallocHost((void**)&d.err_host, sizeof(int)));
     CUDA_TRY(cudaStreamCreateWithFlags(&d.capture, cudaStreamNonBlocking));
+    // per-vertex tent layers (tents are sorted by layer, so each list is ascending)
+    const Mesh& m = *t.mesh;
+    std::vector<int64_t> vt_ptr(m.nv + 1, 0);
+    for (int32_t v : t.vertex) vt_ptr[v + 1]++;
+    for (int64_t v = 0; v < m.nv; ++v) vt_ptr[v + 1] += vt_ptr[v];
+    std::vector<int32_t> vt_layer(t.vertex.size());
+    {
+        std::vector<int64_t> fill(vt_ptr.begin(), vt_ptr.end() - 1);
+        for (size_t i = 0; i < t.vertex.size(); ++i) vt_layer[fill[t.vertex[i]]++] = t.layer[i];
+    }
+    MTP_TRY(upload(&d.tent_layer, t.layer.data(), t.layer.size()));
+    MTP_TRY(upload(&d.vt_ptr, vt_ptr.data(), vt_ptr.size()));
+    MTP_TRY(upload(&d.vt_layer, vt_layer.data(), vt_layer.size()));
+    MTP_TRY(upload(&d.adj_ptr, m.adj_ptr.data(), m.adj_ptr.size()));
+    MTP_TRY(upload(&d.adj, m.adj.data(), m.adj.size()));
+    CUDA_TRY(cudaMalloc((void**)&d.cnt, sizeof(int) * m.nv));
+    CUDA_TRY(cudaMalloc((void**)&d.next, sizeof(unsigned long long)));
     return MTP_OK;
 }
 
@@ -344,6 +370,7 @@ static int check_error_word(Tents& t, cudaStream_t st) {
     CUDA_TRY(cudaStreamSynchronize(st));
     if (*d.err_host == 1) return set_error(MTP_ECAUSAL, "a tent violated |grad phi| < sqrt(eps mu)");
     if (*d.err_host == 2) return set_error(MTP_ENUMERIC, "non-finite value in the evolved state");
+    if (*d.err_host == 3) return set_error(MTP_ETIMEOUT, "a tent's wait for its predecessors exceeded the limit");
     if (*d.err_host != 0) return set_error(MTP_ECUDA, "unknown device error word");
     return MTP_OK;
 }
@@ -376,7 +403,28 @@ int device_evolve(Tents& t, void* state, int64_t lb, int64_t le, bool use_graph,
     CUDA_TRY(cudaMemsetAsync(d.err, 0, sizeof(int), st));
     KArgs a;
     fill_args(t, state, a);
-    if (use_graph && lb == 0 && le == (int64_t)t.layer_ptr.size() - 1) {
+    const bool full = lb == 0 && le == (int64_t)t.layer_ptr.size() - 1;
+    if (use_graph && full && !(m.flags & MTP_FLAG_LAYER_LAUNCHES)) {
+        int bpsm = 0, nsm = 0;
+        CUDA_TRY(ke.persistent_prepare(m.max_patch, &bpsm));
+        CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        const int64_t nt = (int64_t)t.vertex.size();
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)std::max(1, bpsm) * nsm));
+        CUDA_TRY(cudaMemsetAsync(d.cnt, 0, sizeof(int) * m.nv, st));
+        CUDA_TRY(cudaMemsetAsync(d.next, 0, sizeof(unsigned long long), st));
+        PArgs pa;
+        pa.n_tents = nt;
+        pa.next = d.next;
+        pa.cnt = d.cnt;
+        pa.vt_ptr = d.vt_ptr;
+        pa.vt_layer = d.vt_layer;
+        pa.adj_ptr = d.adj_ptr;
+        pa.adj = d.adj;
+        pa.tent_layer = d.tent_layer;
+        pa.timeout_ns = 10000000000LL;     // 10 s per wait
+        pa.n_rhs = m.n_rhs;
+        CUDA_TRY(ke.persistent(a, pa, grid, st));
+    } else if (use_graph && full) {
         if (!d.exec || d.graph_state != state) {
             if (d.exec) { cudaGraphExecDestroy(d.exec); d.exec = nullptr; }
             cudaGraph_t g;

@@ -50,6 +50,7 @@ static int build_mesh(int dim, int64_t nv, const double* X, int64_t ne, const in
     m.m = o.m > 0 ? o.m : 2 * o.p;
     m.precision = o.precision;
     m.n_rhs = o.n_rhs > 0 ? o.n_rhs : 1;
+    m.flags = o.flags;
     m.nf = n_fields(dim);
     m.nb = n_basis(dim, o.p);
     m.nfb = n_face_basis(dim, o.p);
@@ -208,6 +209,23 @@ static int build_mesh(int dim, int64_t nv, const double* X, int64_t ne, const in
                 info[8 + f] = nf;
             }
         }
+    }
+    // vertex adjacency: the other vertices of the elements in each patch
+    m.adj_ptr.assign(nv + 1, 0);
+    {
+        std::vector<std::vector<int32_t>> nb(nv);
+        for (int64_t v = 0; v < nv; ++v) {
+            for (int64_t q = m.patch_ptr[v]; q < m.patch_ptr[v + 1]; ++q) {
+                const int32_t e = m.patch_elem[q];
+                for (int i = 0; i < nvert; ++i)
+                    if (m.elems[(int64_t)e * nvert + i] != v) nb[v].push_back(m.elems[(int64_t)e * nvert + i]);
+            }
+            std::sort(nb[v].begin(), nb[v].end());
+            nb[v].erase(std::unique(nb[v].begin(), nb[v].end()), nb[v].end());
+            m.adj_ptr[v + 1] = m.adj_ptr[v] + (int64_t)nb[v].size();
+        }
+        m.adj.reserve(m.adj_ptr[nv]);
+        for (int64_t v = 0; v < nv; ++v) m.adj.insert(m.adj.end(), nb[v].begin(), nb[v].end());
     }
     const int cap = dim == 2 ? kMaxPatch2D : kMaxPatch3D;
     if (m.max_patch > cap)
@@ -424,7 +442,7 @@ int mtp_mesh_create(int dim, int64_t n_verts, const double* vertices, int64_t n_
     if (opts->q < 0 || opts->m < 0 || opts->q > 8 || opts->m > 64) return set_error(MTP_EINVAL, "q must be in 0..8 and m in 0..64");
     if (opts->precision != MTP_FP64 && opts->precision != MTP_FP32) return set_error(MTP_EINVAL, "unknown precision");
     if (opts->n_rhs < 0 || opts->n_rhs > 4096) return set_error(MTP_EINVAL, "n_rhs must be in 0..4096");
-    if (opts->flags != 0) return set_error(MTP_EINVAL, "flags must be 0");
+    if (opts->flags & ~MTP_FLAG_LAYER_LAUNCHES) return set_error(MTP_EINVAL, "unknown flag bits");
     auto h = std::make_unique<mtp_mesh>();
     int rc = build_mesh(dim, n_verts, vertices, n_elems, elements, eps, mu, *opts, h->m);
     if (rc != MTP_OK) return rc;

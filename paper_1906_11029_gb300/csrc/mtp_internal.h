@@ -44,7 +44,7 @@ RefTables build_ref_tables(int dim, int p);
 constexpr int kGeoStride = 32;
 
 struct Mesh {
-    int dim = 0, p = 0, q = 0, m = 0, precision = 0, n_rhs = 1;
+    int dim = 0, p = 0, q = 0, m = 0, precision = 0, n_rhs = 1, flags = 0;
     int nf = 0, nb = 0, nfb = 0, max_patch = 0;
     int64_t nv = 0, ne = 0;
     std::vector<double> verts;         // [nv][dim]
@@ -59,6 +59,8 @@ struct Mesh {
     // the neighbour across f (-1: PEC boundary facet; -2: f == j), then the neighbour's
     // local facet index.  Packed as 4 bytes + 4 bytes + 4 bytes (3D; 2D pads).
     std::vector<int8_t> patch_info;    // [n_entries][12]
+    std::vector<int64_t> adj_ptr;      // vertex adjacency (CSR, ascending)
+    std::vector<int32_t> adj;
     RefTables ref;
     struct DeviceMesh* dev = nullptr;  // lazily created device copies
 };

@@ -205,7 +205,10 @@ struct TentCtx {
 
 // (a) gather: per-element setup from FP64 geometry and the current front; patch state of
 // `src` into sY (pads zero); U and facet buffers zeroed so their pads stay zero.
-template <typename Real, int DIM, int P>
+template <typename T>
+__device__ __forceinline__ T load_cg(const T* p) { return __ldcg(p); }
+
+template <typename Real, int DIM, int P, bool CG = false>
 __device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t tent, const Real* src) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NV = Sh::NV, NT = Sh::NT, NBP = Sh::NBP;
@@ -225,7 +228,8 @@ __device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t ten
         const double* g = a.geo + (int64_t)e * 32;
         double gp[3] = {0, 0, 0};
         for (int i = 0; i < NV; ++i) {
-            const double tv = (i == j) ? c.tb : a.tau[a.elems[(int64_t)e * NV + i]];
+            const double* tp = a.tau + a.elems[(int64_t)e * NV + i];
+            const double tv = (i == j) ? c.tb : (CG ? load_cg(tp) : *tp);
             for (int q = 0; q < 3; ++q) gp[q] += tv * g[3 * i + q];
         }
         for (int q = 0; q < 3; ++q) {
@@ -250,7 +254,8 @@ __device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t ten
     }
     for (int idx = tid; idx < ns * ESZ; idx += NT) {
         const int k = idx / ESZ, r = idx - k * ESZ, s = r / NBP, b = r - s * NBP;
-        c.sY[idx] = b < NB ? src[((int64_t)a.patch_elem[c.pb + k] * NF + s) * NB + b] : Real(0);
+        const Real* sp = src + ((int64_t)a.patch_elem[c.pb + k] * NF + s) * NB + b;
+        c.sY[idx] = b < NB ? (CG ? load_cg(sp) : *sp) : Real(0);
         c.sUa[idx] = Real(0);
         c.sUb[idx] = Real(0);
     }
@@ -610,6 +615,106 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_layer_kernel(const KAr
     }
     if (bad) atomicExch(a.err, 2);
     if (threadIdx.x == 0 && blockIdx.y == 0) a.tau[c.V] = a.tent_tt[tent];
+}
+
+// Persistent evolve over the whole tent DAG: CTAs pull tents in (layer, vertex) order from a
+// ticket counter; tent s at V waits until every vertex U of {V} u N(V) has completed all its
+// tents of earlier layers (cnt[U] >= number of U's tents with layer < layer(s), found by binary
+// search in U's sorted tent layers), runs all right-hand sides, then publishes cnt[V] += 1.
+// Tickets are only taken by running CTAs and dependencies have smaller tickets, so progress
+// never depends on CTA residency.  Every wait is bounded (globaltimer deadline); on expiry, or
+// when another CTA has already failed, the CTA sets the error word and stops.
+struct PArgs {
+    int64_t n_tents;
+    unsigned long long* next;      // ticket counter
+    int* cnt;                      // completed tents per vertex
+    const int64_t* vt_ptr;         // tents of vertex U: layers vt_layer[vt_ptr[U] .. vt_ptr[U+1])
+    const int32_t* vt_layer;
+    const int64_t* adj_ptr;        // neighbours of U: adj[adj_ptr[U] .. adj_ptr[U+1])
+    const int32_t* adj;
+    const int32_t* tent_layer;
+    long long timeout_ns;
+    int n_rhs;
+};
+
+__device__ __forceinline__ int load_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ long long globaltimer() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename Real, int DIM, int P>
+__global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_persistent_kernel(const KArgs a, const PArgs pa) {
+    using Sh = Shape<DIM, P>;
+    constexpr int NF = Sh::NF, NB = Sh::NB, NT = Sh::NT, NBP = Sh::NBP, ESZ = NF * NBP;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_ticket;
+    __shared__ int s_abort;
+    const SmemLayout<Real, DIM, P> lay(a.max_patch);
+    TentCtx<Real, DIM, P> c;
+    c.carve(smem, lay);
+    while (true) {
+        if (threadIdx.x == 0) {
+            s_ticket = (long long)atomicAdd(pa.next, 1ull);
+            s_abort = 0;
+        }
+        __syncthreads();
+        const long long tent = s_ticket;
+        if (tent >= pa.n_tents) break;
+        // wait for the closed neighbourhood of V (one thread per vertex)
+        const int V = a.tent_v[tent];
+        const int L = pa.tent_layer[tent];
+        const int64_t a0 = pa.adj_ptr[V], deg = pa.adj_ptr[V + 1] - a0;
+        for (int u = threadIdx.x; u <= deg; u += NT) {
+            const int U = u == 0 ? V : pa.adj[a0 + u - 1];
+            int64_t lo = pa.vt_ptr[U], hi = pa.vt_ptr[U + 1];
+            const int64_t base = lo;
+            while (lo < hi) {                      // first tent of U with layer >= L
+                const int64_t mid = (lo + hi) / 2;
+                if (pa.vt_layer[mid] < L) lo = mid + 1; else hi = mid;
+            }
+            const int need = (int)(lo - base);
+            if (load_acquire(pa.cnt + U) < need) {
+                const long long deadline = globaltimer() + pa.timeout_ns;
+                while (load_acquire(pa.cnt + U) < need) {
+                    if (*(volatile int*)a.err != 0 || globaltimer() > deadline) {
+                        atomicCAS(a.err, 0, 3);
+                        s_abort = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+        }
+        __syncthreads();
+        if (s_abort) break;
+        for (int r = 0; r < pa.n_rhs; ++r) {
+            Real* state = (Real*)a.state + (int64_t)r * a.rhs_stride;
+            tent_setup<Real, DIM, P, true>(c, a, tent, state);
+            tent_sat(c, a, (Real*)nullptr);
+            bool bad = false;
+            for (int idx = threadIdx.x; idx < c.ns * NF * NB; idx += NT) {
+                const int k = idx / (NF * NB), rr = idx - k * NF * NB, s = rr / NB, b = rr - s * NB;
+                const Real v = c.sY[k * ESZ + s * NBP + b];
+                if (!isfinite((double)v)) bad = true;
+                state[(int64_t)a.patch_elem[c.pb + k] * NF * NB + rr] = v;
+            }
+            if (bad) atomicExch(a.err, 2);
+            __threadfence();                       // publish this thread's state writes (gpu scope)
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            a.tau[V] = a.tent_tt[tent];
+            __threadfence();
+            atomicAdd(pa.cnt + V, 1);
+        }
+        __syncthreads();
+    }
 }
 
 }  // namespace mtp

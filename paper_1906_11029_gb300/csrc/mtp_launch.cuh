@@ -8,6 +8,8 @@ namespace mtp {
 
 using LaunchFn = cudaError_t (*)(const KArgs&, int64_t t0, int n_tents, int n_rhs, cudaStream_t st);
 using PrepareFn = cudaError_t (*)(int max_patch, size_t* smem_bytes);
+using PersistentFn = cudaError_t (*)(const KArgs&, const PArgs&, int grid, cudaStream_t st);
+using PersistentPrepFn = cudaError_t (*)(int max_patch, int* blocks_per_sm);
 
 template <typename Real, int DIM, int P>
 cudaError_t prepare_tent_kernel(int max_patch, size_t* smem_bytes) {
@@ -25,9 +27,28 @@ cudaError_t launch_tent_kernel(const KArgs& a, int64_t t0, int n_tents, int n_rh
     return cudaGetLastError();
 }
 
+template <typename Real, int DIM, int P>
+cudaError_t prepare_persistent_kernel(int max_patch, int* blocks_per_sm) {
+    SmemLayout<Real, DIM, P> lay(max_patch);
+    cudaError_t e = cudaFuncSetAttribute(tent_persistent_kernel<Real, DIM, P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.bytes);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tent_persistent_kernel<Real, DIM, P>,
+                                                         Shape<DIM, P>::NT, lay.bytes);
+}
+
+template <typename Real, int DIM, int P>
+cudaError_t launch_persistent_kernel(const KArgs& a, const PArgs& pa, int grid, cudaStream_t st) {
+    SmemLayout<Real, DIM, P> lay(a.max_patch);
+    tent_persistent_kernel<Real, DIM, P><<<grid, Shape<DIM, P>::NT, lay.bytes, st>>>(a, pa);
+    return cudaGetLastError();
+}
+
 struct KernelEntry {
     LaunchFn launch;
     PrepareFn prepare;
+    PersistentFn persistent;
+    PersistentPrepFn persistent_prepare;
 };
 
 // entries[dim - 2][p - 1]
@@ -47,14 +68,22 @@ void adjoint_table(AdjEntry entries[2][2][4]);
 
 #define MTP_KERNEL_TABLE(NAME, REAL)                                                   \
     void NAME(KernelEntry e[2][4]) {                                                   \
-        e[0][0] = {launch_tent_kernel<REAL, 2, 1>, prepare_tent_kernel<REAL, 2, 1>};   \
-        e[0][1] = {launch_tent_kernel<REAL, 2, 2>, prepare_tent_kernel<REAL, 2, 2>};   \
-        e[0][2] = {launch_tent_kernel<REAL, 2, 3>, prepare_tent_kernel<REAL, 2, 3>};   \
-        e[0][3] = {launch_tent_kernel<REAL, 2, 4>, prepare_tent_kernel<REAL, 2, 4>};   \
-        e[1][0] = {launch_tent_kernel<REAL, 3, 1>, prepare_tent_kernel<REAL, 3, 1>};   \
-        e[1][1] = {launch_tent_kernel<REAL, 3, 2>, prepare_tent_kernel<REAL, 3, 2>};   \
-        e[1][2] = {launch_tent_kernel<REAL, 3, 3>, prepare_tent_kernel<REAL, 3, 3>};   \
-        e[1][3] = {launch_tent_kernel<REAL, 3, 4>, prepare_tent_kernel<REAL, 3, 4>};   \
+        e[0][0] = {launch_tent_kernel<REAL, 2, 1>, prepare_tent_kernel<REAL, 2, 1>, \
+                    launch_persistent_kernel<REAL, 2, 1>, prepare_persistent_kernel<REAL, 2, 1>};   \
+        e[0][1] = {launch_tent_kernel<REAL, 2, 2>, prepare_tent_kernel<REAL, 2, 2>, \
+                    launch_persistent_kernel<REAL, 2, 2>, prepare_persistent_kernel<REAL, 2, 2>};   \
+        e[0][2] = {launch_tent_kernel<REAL, 2, 3>, prepare_tent_kernel<REAL, 2, 3>, \
+                    launch_persistent_kernel<REAL, 2, 3>, prepare_persistent_kernel<REAL, 2, 3>};   \
+        e[0][3] = {launch_tent_kernel<REAL, 2, 4>, prepare_tent_kernel<REAL, 2, 4>, \
+                    launch_persistent_kernel<REAL, 2, 4>, prepare_persistent_kernel<REAL, 2, 4>};   \
+        e[1][0] = {launch_tent_kernel<REAL, 3, 1>, prepare_tent_kernel<REAL, 3, 1>, \
+                    launch_persistent_kernel<REAL, 3, 1>, prepare_persistent_kernel<REAL, 3, 1>};   \
+        e[1][1] = {launch_tent_kernel<REAL, 3, 2>, prepare_tent_kernel<REAL, 3, 2>, \
+                    launch_persistent_kernel<REAL, 3, 2>, prepare_persistent_kernel<REAL, 3, 2>};   \
+        e[1][2] = {launch_tent_kernel<REAL, 3, 3>, prepare_tent_kernel<REAL, 3, 3>, \
+                    launch_persistent_kernel<REAL, 3, 3>, prepare_persistent_kernel<REAL, 3, 3>};   \
+        e[1][3] = {launch_tent_kernel<REAL, 3, 4>, prepare_tent_kernel<REAL, 3, 4>, \
+                    launch_persistent_kernel<REAL, 3, 4>, prepare_persistent_kernel<REAL, 3, 4>};   \
     }
 
 }  // namespace mtp

@@ -163,3 +163,19 @@ def test_pitcher_on_device_box_matches_oracle():
     for k in ("vertex", "layer", "layer_ptr"):
         assert np.array_equal(got[k], ref[k])
     assert np.array_equal(got["t_top"].view(np.uint64), ref["t_top"].view(np.uint64))
+
+
+@pytest.mark.parametrize("name", ["cube_n2_p3", "te_square_n8_p2"])
+def test_persistent_dag_walk_equals_layer_launches(name):
+    """The persistent DAG-walking evolve and the per-layer launches apply the same tent maps:
+    FP64 results are bit-identical (each tent's arithmetic does not depend on scheduling)."""
+    w = _CASES[name]()
+    vals0, _, _, _ = _oracle(name)
+    outs = []
+    for flags in (0, mtp.MTP_FLAG_LAYER_LAUNCHES):
+        m = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, n_rhs=2, flags=flags)
+        t = m.pitch(w.T)
+        st = m.state_from_lattice(torch.tensor(np.stack([vals0, 2 * vals0]), device=DEV))
+        t.evolve(st)
+        outs.append(st.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
