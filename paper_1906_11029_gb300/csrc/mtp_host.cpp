@@ -183,6 +183,19 @@ static int build_mesh(int dim, int64_t nv, const double* X, int64_t ne, const in
     }
     m.max_patch = 0;
     m.patch_info.assign(m.patch_elem.size() * 12, 0);
+    // order each patch by (local index of V, element id): elements sharing the lambda_V-weighted
+    // reference tables are adjacent, so the tent kernel can pair them
+    auto local_index = [&](int32_t e, int64_t v) {
+        int j = 0;
+        while (m.elems[(int64_t)e * nvert + j] != v) ++j;
+        return j;
+    };
+    for (int64_t v = 0; v < nv; ++v)
+        std::stable_sort(m.patch_elem.begin() + m.patch_ptr[v], m.patch_elem.begin() + m.patch_ptr[v + 1],
+                         [&](int32_t x, int32_t y) {
+                             const int jx = local_index(x, v), jy = local_index(y, v);
+                             return jx != jy ? jx < jy : x < y;
+                         });
     for (int64_t v = 0; v < nv; ++v) {
         int64_t b = m.patch_ptr[v], n = m.patch_ptr[v + 1] - b;
         m.max_patch = std::max<int>(m.max_patch, (int)n);

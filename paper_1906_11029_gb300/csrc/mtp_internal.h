@@ -54,7 +54,7 @@ struct Mesh {
     std::vector<int32_t> nbr;          // [ne][dim+1] neighbour element or -1 (PEC)
     std::vector<int8_t> nbr_face;      // [ne][dim+1] neighbour's local facet
     std::vector<int64_t> patch_ptr;    // [nv+1]
-    std::vector<int32_t> patch_elem;   // elements of omega_V, ascending
+    std::vector<int32_t> patch_elem;   // elements of omega_V, ordered by (local index of V, id)
     // per patch entry: local index j of V, then for each local facet f the patch slot of
     // the neighbour across f (-1: PEC boundary facet; -2: f == j), then the neighbour's
     // local facet index.  Packed as 4 bytes + 4 bytes + 4 bytes (3D; 2D pads).

@@ -71,6 +71,13 @@ struct Shape {
     static constexpr int NCG = (NFB + AP - 1) / AP;    // facet-mode groups per facet
 };
 
+// CTAs per SM the register budget is shaped for (two 256-thread CTAs fit the FP32 3D
+// shared-memory footprint up to p = 4; FP64 p >= 3 fits one)
+template <typename Real, int DIM, int P>
+struct MinBlocks {
+    static constexpr int value = (sizeof(Real) == 4 || P <= 2) ? 2 : 1;
+};
+
 template <typename Real>
 struct Vec;
 template <>
@@ -92,7 +99,7 @@ struct SmemLayout {
     using Sh = Shape<DIM, P>;
     static __host__ __device__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
     size_t off_Y, off_Ua, off_Ub, off_tr, off_Gi, off_gphi, off_gdel, off_mat, off_ac, off_gd, off_nrm,
-        off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, bytes, state_bytes, tr_bytes;
+        off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, off_pair, bytes, state_bytes, tr_bytes;
     __host__ __device__ explicit SmemLayout(int mp) {
         size_t o = 0;
         state_bytes = (size_t)mp * Sh::NF * Sh::NBP * sizeof(Real);
@@ -114,6 +121,7 @@ struct SmemLayout {
         off_j = o; o = align16(o + (size_t)mp);
         off_nslot = o; o = align16(o + (size_t)mp * DIM);
         off_nfi = o; o = align16(o + (size_t)mp * DIM);
+        off_pair = o; o = align16(o + (size_t)mp * 2 + 4);
         bytes = o;
     }
 };
@@ -177,7 +185,8 @@ struct TentCtx {
     Real *sY, *sUa, *sUb, *sTr, *sGi;
     double *sGphi, *sGdel, *sMat;
     Real *sAc, *sGd, *sNrm, *sLiftc, *sTrs, *sZ;
-    int8_t *sJ, *sNslot, *sNfi;
+    int8_t *sJ, *sNslot, *sNfi, *sPair;   // sPair: [pair][2] element slots (second -1: single)
+    int* sNpair;
     int V, ns;
     int64_t pb;
     double tb, dt;
@@ -200,6 +209,8 @@ struct TentCtx {
         sJ = (int8_t*)(smem + lay.off_j);
         sNslot = (int8_t*)(smem + lay.off_nslot);
         sNfi = (int8_t*)(smem + lay.off_nfi);
+        sPair = (int8_t*)(smem + lay.off_pair + 4);
+        sNpair = (int*)(smem + lay.off_pair);
     }
 };
 
@@ -280,6 +291,17 @@ __device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t ten
             ++fi;
         }
     }
+    if (tid == 0) {   // pairs of consecutive elements with the same local index of V
+        int np = 0;
+        for (int k = 0; k < ns;) {
+            const bool pair = k + 1 < ns && c.sJ[k + 1] == c.sJ[k];
+            c.sPair[2 * np] = (int8_t)k;
+            c.sPair[2 * np + 1] = pair ? (int8_t)(k + 1) : (int8_t)-1;
+            ++np;
+            k += pair ? 2 : 1;
+        }
+        *c.sNpair = np;
+    }
     __syncthreads();
 }
 
@@ -324,7 +346,8 @@ __device__ void tent_apply_ginv(TentCtx<Real, DIM, P>& c, const Real* src, Real*
     }
 }
 
-// (b1) facet traces of U on the facets containing V, two modes per thread, into tr
+// (b1) facet traces of U on the facets containing V: one thread per (element, two facet
+// modes), all DIM facets, so every 16-byte read of U feeds DIM x 2 x W FMAs
 template <typename Real, int DIM, int P>
 __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real* Ucur, Real* tr) {
     using Sh = Shape<DIM, P>;
@@ -332,42 +355,54 @@ __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real
     constexpr int NF = Sh::NF, NFB = Sh::NFB, NT = Sh::NT, NBP = Sh::NBP, NFBP = Sh::NFBP;
     constexpr int AP = Sh::AP, NCG = Sh::NCG, W = Vec<Real>::W, ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
     const Real* Tr = (const Real*)a.Tr;
-    for (int idx = threadIdx.x; idx < c.ns * DIM * NCG; idx += NT) {
-        const int k = idx / (DIM * NCG), rem = idx - k * DIM * NCG, fi = rem / NCG;
-        const int c0 = (rem - fi * NCG) * AP;
-        const int j = c.sJ[k];
-        const int f = fi + (fi >= j ? 1 : 0);
-        const Real* U = Ucur + k * ESZ;
-        const Real* T0 = Tr + ((size_t)f * NFB + c0) * NBP;
+    for (int idx = threadIdx.x; idx < c.ns * NCG; idx += NT) {
+        const int k = idx / NCG;
+        const int c0 = (idx - k * NCG) * AP;
         const bool two = c0 + 1 < NFB;
-        const Real* T1 = two ? T0 + NBP : T0;
-        Real acc[AP][NF];
+        const int j = c.sJ[k];
+        const Real* U = Ucur + k * ESZ;
+        const Real* T[DIM][AP];
 #pragma unroll
-        for (int ci = 0; ci < AP; ++ci)
+        for (int fi = 0; fi < DIM; ++fi) {
+            const int f = fi + (fi >= j ? 1 : 0);
+            T[fi][0] = Tr + ((size_t)f * NFB + c0) * NBP;
+            T[fi][1] = two ? T[fi][0] + NBP : T[fi][0];
+        }
+        Real acc[DIM][AP][NF];
 #pragma unroll
-            for (int s = 0; s < NF; ++s) acc[ci][s] = 0;
+        for (int fi = 0; fi < DIM; ++fi)
+#pragma unroll
+            for (int ci = 0; ci < AP; ++ci)
+#pragma unroll
+                for (int s = 0; s < NF; ++s) acc[fi][ci][s] = 0;
 #pragma unroll 1
         for (int b = 0; b < NBP; b += W) {
-            Real t0v[W], t1v[W];
-            Vec<Real>::get(__ldg((const VT*)(T0 + b)), t0v);
-            Vec<Real>::get(__ldg((const VT*)(T1 + b)), t1v);
+            Real tv[DIM][AP][W];
+#pragma unroll
+            for (int fi = 0; fi < DIM; ++fi)
+#pragma unroll
+                for (int ci = 0; ci < AP; ++ci) Vec<Real>::get(__ldg((const VT*)(T[fi][ci] + b)), tv[fi][ci]);
 #pragma unroll
             for (int s = 0; s < NF; ++s) {
                 Real u[W];
                 Vec<Real>::get(*(const VT*)(U + s * NBP + b), u);
 #pragma unroll
-                for (int v = 0; v < W; ++v) {
-                    acc[0][s] += t0v[v] * u[v];
-                    acc[1][s] += t1v[v] * u[v];
-                }
+                for (int v = 0; v < W; ++v)
+#pragma unroll
+                    for (int fi = 0; fi < DIM; ++fi)
+#pragma unroll
+                        for (int ci = 0; ci < AP; ++ci) acc[fi][ci][s] += tv[fi][ci][v] * u[v];
             }
         }
         const Real sc = c.sTrs[k];
-        Real* out = tr + k * TSZ + fi * NF * NFBP + c0;
 #pragma unroll
-        for (int s = 0; s < NF; ++s) {
-            out[s * NFBP] = acc[0][s] * sc;
-            if (two) out[s * NFBP + 1] = acc[1][s] * sc;
+        for (int fi = 0; fi < DIM; ++fi) {
+            Real* out = tr + k * TSZ + fi * NF * NFBP + c0;
+#pragma unroll
+            for (int s = 0; s < NF; ++s) {
+                out[s * NFBP] = acc[fi][0][s] * sc;
+                if (two) out[s * NFBP + 1] = acc[fi][1][s] * sc;
+            }
         }
     }
 }
@@ -409,7 +444,9 @@ __device__ void tent_fluxes(TentCtx<Real, DIM, P>& c, Real* tr) {
 }
 
 // (b3)+(c) Y_{i,n} = A U_{i,n-1} (volume + lift of the scaled fluxes in tr), Taylor
-// accumulation into sY, and U_{i,n} = G_i^-1 (Y_{i,n} - n M' U_{i,n-1}) into Unext (n < q)
+// accumulation into sY, and U_{i,n} = G_i^-1 (Y_{i,n} - n M' U_{i,n-1}) into Unext (n < q).
+// One thread per (pair of elements with the same local index j, two basis functions): every
+// 16-byte read of the j-dependent tables S and L feeds both elements.
 template <typename Real, int DIM, int P>
 __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, const Real* Ucur, Real* Unext,
                            const Real* tr) {
@@ -417,142 +454,172 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
     using VT = typename Vec<Real>::T;
     constexpr int NF = Sh::NF, NB = Sh::NB, NV = Sh::NV, NT = Sh::NT, NBP = Sh::NBP, NFBP = Sh::NFBP;
     constexpr int AP = Sh::AP, NAG = Sh::NAG, W = Vec<Real>::W, ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
+    constexpr int EP = sizeof(Real) == 4 ? 2 : 1;   // elements per thread (FP64: register budget)
     const Real* S = (const Real*)a.S;
     const Real* Lf = (const Real*)a.L;
     const Real cn = (Real)a.taylor[n];
     const Real nn = (Real)n;
-    for (int idx = threadIdx.x; idx < c.ns * NAG; idx += NT) {
-        const int k = idx / NAG, a0 = (idx - k * NAG) * AP;
+    const int nitems = EP == 2 ? *c.sNpair : c.ns;   // pairs, or single elements
+    for (int idx = threadIdx.x; idx < nitems * NAG; idx += NT) {
+        const int pi = idx / NAG, a0 = (idx - pi * NAG) * AP;
         const bool two = a0 + 1 < NB;
-        const int j = c.sJ[k];
-        const Real* U = Ucur + k * ESZ;
-        Real Pm[AP][DIM][NF];
+        const int k0 = EP == 2 ? c.sPair[2 * pi] : pi;
+        const int kk1 = EP == 2 ? c.sPair[2 * pi + 1] : -1;
+        const bool has1 = kk1 >= 0;
+        int kk[2] = {k0, has1 ? kk1 : k0};
+        const int j = c.sJ[k0];
+        Real Yn[EP][AP][NF];
+        {
+            Real Pm[EP][AP][DIM][NF];
 #pragma unroll
-        for (int ai = 0; ai < AP; ++ai)
+            for (int e = 0; e < EP; ++e)
 #pragma unroll
-            for (int l = 0; l < DIM; ++l)
+                for (int ai = 0; ai < AP; ++ai)
 #pragma unroll
-                for (int s = 0; s < NF; ++s) Pm[ai][l][s] = 0;
-        const Real* S0 = S + ((size_t)j * DIM * NB + a0) * NBP;
-        const Real* S1 = two ? S0 + NBP : S0;
+                    for (int l = 0; l < DIM; ++l)
+#pragma unroll
+                        for (int s = 0; s < NF; ++s) Pm[e][ai][l][s] = 0;
+            const Real* S0 = S + ((size_t)j * DIM * NB + a0) * NBP;
+            const Real* S1 = two ? S0 + NBP : S0;
 #pragma unroll 1
-        for (int b = 0; b < NBP; b += W) {
-            Real sv[AP][DIM][W];
-#pragma unroll
-            for (int l = 0; l < DIM; ++l) {
-                Vec<Real>::get(__ldg((const VT*)(S0 + (size_t)l * NB * NBP + b)), sv[0][l]);
-                Vec<Real>::get(__ldg((const VT*)(S1 + (size_t)l * NB * NBP + b)), sv[1][l]);
-            }
-#pragma unroll
-            for (int s = 0; s < NF; ++s) {
-                Real u[W];
-                Vec<Real>::get(*(const VT*)(U + s * NBP + b), u);
-#pragma unroll
-                for (int v = 0; v < W; ++v)
-#pragma unroll
-                    for (int ai = 0; ai < AP; ++ai)
-#pragma unroll
-                        for (int l = 0; l < DIM; ++l) Pm[ai][l][s] += sv[ai][l][v] * u[v];
-            }
-        }
-        Real Yn[AP][NF];
-        const Real* ac = c.sAc + k * DIM * 3;
-#pragma unroll
-        for (int ai = 0; ai < AP; ++ai) {
-            if constexpr (DIM == 3) {
-                Real vE[3] = {0, 0, 0}, vH[3] = {0, 0, 0};
+            for (int b = 0; b < NBP; b += W) {
+                Real sv[AP][DIM][W];
 #pragma unroll
                 for (int l = 0; l < DIM; ++l) {
-                    const Real ax = ac[3 * l], ay = ac[3 * l + 1], az = ac[3 * l + 2];
-                    const Real* Pl = Pm[ai][l];
-                    vE[0] -= ay * Pl[5] - az * Pl[4];   // -a x P_H
-                    vE[1] -= az * Pl[3] - ax * Pl[5];
-                    vE[2] -= ax * Pl[4] - ay * Pl[3];
-                    vH[0] += ay * Pl[2] - az * Pl[1];   //  a x P_E
-                    vH[1] += az * Pl[0] - ax * Pl[2];
-                    vH[2] += ax * Pl[1] - ay * Pl[0];
+                    Vec<Real>::get(__ldg((const VT*)(S0 + (size_t)l * NB * NBP + b)), sv[0][l]);
+                    Vec<Real>::get(__ldg((const VT*)(S1 + (size_t)l * NB * NBP + b)), sv[1][l]);
                 }
 #pragma unroll
-                for (int q = 0; q < 3; ++q) { Yn[ai][q] = vE[q]; Yn[ai][3 + q] = vH[q]; }
-            } else {
-                Real ex = 0, ey = 0, hz = 0;
+                for (int e = 0; e < EP; ++e) {
+                    const Real* U = Ucur + kk[e] * ESZ;
 #pragma unroll
-                for (int l = 0; l < DIM; ++l) {
-                    const Real ax = ac[3 * l], ay = ac[3 * l + 1];
-                    const Real* Pl = Pm[ai][l];
-                    ex -= ay * Pl[2];
-                    ey += ax * Pl[2];
-                    hz += ax * Pl[1] - ay * Pl[0];
+                    for (int s = 0; s < NF; ++s) {
+                        Real u[W];
+                        Vec<Real>::get(*(const VT*)(U + s * NBP + b), u);
+#pragma unroll
+                        for (int v = 0; v < W; ++v)
+#pragma unroll
+                            for (int ai = 0; ai < AP; ++ai)
+#pragma unroll
+                                for (int l = 0; l < DIM; ++l) Pm[e][ai][l][s] += sv[ai][l][v] * u[v];
+                    }
                 }
-                Yn[ai][0] = ex; Yn[ai][1] = ey; Yn[ai][2] = hz;
+            }
+#pragma unroll
+            for (int e = 0; e < EP; ++e) {
+                const Real* ac = c.sAc + kk[e] * DIM * 3;
+#pragma unroll
+                for (int ai = 0; ai < AP; ++ai) {
+                    if constexpr (DIM == 3) {
+                        Real vE[3] = {0, 0, 0}, vH[3] = {0, 0, 0};
+#pragma unroll
+                        for (int l = 0; l < DIM; ++l) {
+                            const Real ax = ac[3 * l], ay = ac[3 * l + 1], az = ac[3 * l + 2];
+                            const Real* Pl = Pm[e][ai][l];
+                            vE[0] -= ay * Pl[5] - az * Pl[4];   // -a x P_H
+                            vE[1] -= az * Pl[3] - ax * Pl[5];
+                            vE[2] -= ax * Pl[4] - ay * Pl[3];
+                            vH[0] += ay * Pl[2] - az * Pl[1];   //  a x P_E
+                            vH[1] += az * Pl[0] - ax * Pl[2];
+                            vH[2] += ax * Pl[1] - ay * Pl[0];
+                        }
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) { Yn[e][ai][q] = vE[q]; Yn[e][ai][3 + q] = vH[q]; }
+                    } else {
+                        Real ex = 0, ey = 0, hz = 0;
+#pragma unroll
+                        for (int l = 0; l < DIM; ++l) {
+                            const Real ax = ac[3 * l], ay = ac[3 * l + 1];
+                            const Real* Pl = Pm[e][ai][l];
+                            ex -= ay * Pl[2];
+                            ey += ax * Pl[2];
+                            hz += ax * Pl[1] - ay * Pl[0];
+                        }
+                        Yn[e][ai][0] = ex; Yn[e][ai][1] = ey; Yn[e][ai][2] = hz;
+                    }
+                }
             }
         }
-        // lift of the (already scaled) facet fluxes
+        // lift of the (already scaled) facet fluxes; the facet of local index f is the same for
+        // both elements (same j)
 #pragma unroll
         for (int fi = 0; fi < DIM; ++fi) {
             const int f = fi + (fi >= j ? 1 : 0);
             const Real* L0 = Lf + (((size_t)j * NV + f) * NB + a0) * NFBP;
             const Real* L1 = two ? L0 + NFBP : L0;
-            const Real* Fx = tr + k * TSZ + fi * NF * NFBP;
-            Real acc[AP][NF];
+            Real acc[EP][AP][NF];
 #pragma unroll
-            for (int ai = 0; ai < AP; ++ai)
+            for (int e = 0; e < EP; ++e)
 #pragma unroll
-                for (int s = 0; s < NF; ++s) acc[ai][s] = 0;
+                for (int ai = 0; ai < AP; ++ai)
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) acc[e][ai][s] = 0;
 #pragma unroll
             for (int cc = 0; cc < NFBP; cc += W) {
                 Real l0[W], l1[W];
                 Vec<Real>::get(__ldg((const VT*)(L0 + cc)), l0);
                 Vec<Real>::get(__ldg((const VT*)(L1 + cc)), l1);
 #pragma unroll
-                for (int s = 0; s < NF; ++s) {
-                    Real fv[W];
-                    Vec<Real>::get(*(const VT*)(Fx + s * NFBP + cc), fv);
+                for (int e = 0; e < EP; ++e) {
+                    const Real* Fx = tr + kk[e] * TSZ + fi * NF * NFBP;
 #pragma unroll
-                    for (int v = 0; v < W; ++v) {
-                        acc[0][s] += l0[v] * fv[v];
-                        acc[1][s] += l1[v] * fv[v];
+                    for (int s = 0; s < NF; ++s) {
+                        Real fv[W];
+                        Vec<Real>::get(*(const VT*)(Fx + s * NFBP + cc), fv);
+#pragma unroll
+                        for (int v = 0; v < W; ++v) {
+                            acc[e][0][s] += l0[v] * fv[v];
+                            acc[e][1][s] += l1[v] * fv[v];
+                        }
                     }
                 }
             }
 #pragma unroll
-            for (int ai = 0; ai < AP; ++ai)
+            for (int e = 0; e < EP; ++e)
 #pragma unroll
-                for (int s = 0; s < NF; ++s) Yn[ai][s] -= acc[ai][s];
+                for (int ai = 0; ai < AP; ++ai)
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) Yn[e][ai][s] -= acc[e][ai][s];
         }
-        const Real* gd = c.sGd + 3 * k;
-        const Real* Gi = c.sGi + k * NF * NF;
 #pragma unroll
-        for (int ai = 0; ai < AP; ++ai) {
-            if (ai == 1 && !two) break;
-            const int av = a0 + ai;
+        for (int e = 0; e < EP; ++e) {
+            if (e == 1 && !has1) break;
+            const int k = kk[e];
+            const Real* U = Ucur + k * ESZ;
+            const Real* gd = c.sGd + 3 * k;
+            const Real* Gi = c.sGi + k * NF * NF;
 #pragma unroll
-            for (int s = 0; s < NF; ++s) c.sY[k * ESZ + s * NBP + av] += cn * Yn[ai][s];
-            if (n < a.q) {
-                Real r6[NF];
-                if constexpr (DIM == 3) {
-                    const Real E0 = U[0 * NBP + av], E1 = U[1 * NBP + av], E2 = U[2 * NBP + av];
-                    const Real H0 = U[3 * NBP + av], H1 = U[4 * NBP + av], H2 = U[5 * NBP + av];
-                    // M'U = [-H x gd ; E x gd]
-                    r6[0] = Yn[ai][0] + nn * (H1 * gd[2] - H2 * gd[1]);
-                    r6[1] = Yn[ai][1] + nn * (H2 * gd[0] - H0 * gd[2]);
-                    r6[2] = Yn[ai][2] + nn * (H0 * gd[1] - H1 * gd[0]);
-                    r6[3] = Yn[ai][3] - nn * (E1 * gd[2] - E2 * gd[1]);
-                    r6[4] = Yn[ai][4] - nn * (E2 * gd[0] - E0 * gd[2]);
-                    r6[5] = Yn[ai][5] - nn * (E0 * gd[1] - E1 * gd[0]);
-                } else {
-                    const Real Ex = U[0 * NBP + av], Ey = U[1 * NBP + av], Hz = U[2 * NBP + av];
-                    // M'U (TE) = (Hz gy, -Hz gx, Ex gy - Ey gx)
-                    r6[0] = Yn[ai][0] - nn * (Hz * gd[1]);
-                    r6[1] = Yn[ai][1] + nn * (Hz * gd[0]);
-                    r6[2] = Yn[ai][2] - nn * (Ex * gd[1] - Ey * gd[0]);
-                }
+            for (int ai = 0; ai < AP; ++ai) {
+                if (ai == 1 && !two) break;
+                const int av = a0 + ai;
 #pragma unroll
-                for (int r = 0; r < NF; ++r) {
-                    Real acc = 0;
+                for (int s = 0; s < NF; ++s) c.sY[k * ESZ + s * NBP + av] += cn * Yn[e][ai][s];
+                if (n < a.q) {
+                    Real r6[NF];
+                    if constexpr (DIM == 3) {
+                        const Real E0 = U[0 * NBP + av], E1 = U[1 * NBP + av], E2 = U[2 * NBP + av];
+                        const Real H0 = U[3 * NBP + av], H1 = U[4 * NBP + av], H2 = U[5 * NBP + av];
+                        // M'U = [-H x gd ; E x gd]
+                        r6[0] = Yn[e][ai][0] + nn * (H1 * gd[2] - H2 * gd[1]);
+                        r6[1] = Yn[e][ai][1] + nn * (H2 * gd[0] - H0 * gd[2]);
+                        r6[2] = Yn[e][ai][2] + nn * (H0 * gd[1] - H1 * gd[0]);
+                        r6[3] = Yn[e][ai][3] - nn * (E1 * gd[2] - E2 * gd[1]);
+                        r6[4] = Yn[e][ai][4] - nn * (E2 * gd[0] - E0 * gd[2]);
+                        r6[5] = Yn[e][ai][5] - nn * (E0 * gd[1] - E1 * gd[0]);
+                    } else {
+                        const Real Ex = U[0 * NBP + av], Ey = U[1 * NBP + av], Hz = U[2 * NBP + av];
+                        // M'U (TE) = (Hz gy, -Hz gx, Ex gy - Ey gx)
+                        r6[0] = Yn[e][ai][0] - nn * (Hz * gd[1]);
+                        r6[1] = Yn[e][ai][1] + nn * (Hz * gd[0]);
+                        r6[2] = Yn[e][ai][2] - nn * (Ex * gd[1] - Ey * gd[0]);
+                    }
 #pragma unroll
-                    for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * r6[s];
-                    Unext[k * ESZ + r * NBP + av] = acc;
+                    for (int r = 0; r < NF; ++r) {
+                        Real acc = 0;
+#pragma unroll
+                        for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * r6[s];
+                        Unext[k * ESZ + r * NBP + av] = acc;
+                    }
                 }
             }
         }
@@ -594,7 +661,7 @@ __device__ void tent_sat(TentCtx<Real, DIM, P>& c, const KArgs& a, Real* tape) {
 }
 
 template <typename Real, int DIM, int P>
-__global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_layer_kernel(const KArgs a, int64_t t0) {
+__global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::value) tent_layer_kernel(const KArgs a, int64_t t0) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NT = Sh::NT, NBP = Sh::NBP, ESZ = NF * NBP;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -649,7 +716,7 @@ __device__ __forceinline__ long long globaltimer() {
 }
 
 template <typename Real, int DIM, int P>
-__global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_persistent_kernel(const KArgs a, const PArgs pa) {
+__global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::value) tent_persistent_kernel(const KArgs a, const PArgs pa) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NT = Sh::NT, NBP = Sh::NBP, ESZ = NF * NBP;
     extern __shared__ __align__(16) unsigned char smem[];
