@@ -36,7 +36,8 @@ N_SMS = 152
 # DRAM bytes (read + write) per tent of the FP32 p=4 tent kernel from the last ncu capture of
 # the current kernel version (profiles/tent_layer_kernel_fp32_p4_graded32.md); None once the
 # kernel has changed since the counters were taken.
-TRAFFIC_BYTES_PER_TENT = {"fp32": 27526.0}
+TRAFFIC_BYTES_PER_TENT = {"fp32": 27526.0}          # tent_layer_kernel, per tent
+TRAFFIC_PERSISTENT_BYTES = {}                         # tent_persistent_kernel, per tent (not captured yet)
 
 
 def load_peaks():
@@ -203,6 +204,20 @@ def run_profile(args):
         np.diff(tents.get()["layer_ptr"][a:b + 1]))), "workload": w.name}))
 
 
+def run_profile_evolve(args):
+    """Profiling driver: build the workload and run one full evolve (the persistent kernel)."""
+    import torch
+    import paper_1906_11029_gb300 as mtp
+    w = make_workload(args.workload)
+    prec = mtp.MTP_FP32 if args.precision == "fp32" else mtp.MTP_FP64
+    mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=prec)
+    tents = mesh.pitch(w.T, w.causality)
+    state = mesh.state_from_lattice(torch.tensor(initial_lattice(w)[None], device="cuda"))
+    tents.evolve(state)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_evolve": w.name, "tents": tents.info["n_tents"]}))
+
+
 def run_mtp(args):
     import torch
     import paper_1906_11029_gb300 as mtp
@@ -280,8 +295,9 @@ def run_mtp(args):
         peak = args.fp64_peak_tflops
         bound = "alu"
     achieved = flops_per_launch / (launch_ms / 1e3) / 1e12
-    tpl = TRAFFIC_BYTES_PER_TENT.get(args.precision) if args.workload == "graded" else None
-    traffic = None if tpl is None else tpl * tents.info["n_tents"] / launches_per_step
+    tpl = (TRAFFIC_BYTES_PER_TENT.get(args.precision)
+           if args.workload == "graded" and not persistent else TRAFFIC_PERSISTENT_BYTES.get(args.precision))
+    traffic = None if tpl is None or args.workload != "graded" else tpl * tents.info["n_tents"] / launches_per_step
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": (f"tent_persistent_kernel<{args.precision},3,{w.p}>" if persistent
@@ -379,6 +395,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", default=None)
     ap.add_argument("--profile-window", default=None, help="a:b -> apply layers [a, b) once and exit")
+    ap.add_argument("--profile-evolve", action="store_true", help="run one full evolve and exit")
     ap.add_argument("--seed", type=int, default=7)
     args = ap.parse_args()
     if args.cpu_worker:
@@ -387,6 +404,8 @@ def main():
         return run_reference(args)
     if args.profile_window:
         return run_profile(args)
+    if args.profile_evolve:
+        return run_profile_evolve(args)
     return run_mtp(args)
 
 

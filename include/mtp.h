@@ -59,6 +59,7 @@ extern "C" {
 
 typedef struct mtp_mesh*  mtp_mesh_t;
 typedef struct mtp_tents* mtp_tents_t;
+typedef struct mtp_batch* mtp_batch_t;
 
 typedef struct {
     int p;          /* polynomial degree of V_h, 1..4 (Sec. 3, DG space)                   */
@@ -144,6 +145,20 @@ int mtp_evolve_layers(mtp_tents_t tents, void* state_dev, int64_t layer_begin,
  * synchronises the stream before returning.  state_in_host may equal state_out_host. */
 int mtp_evolve_host(mtp_tents_t tents, const void* state_in_host, void* state_out_host,
                     double T, void* stream);
+
+/* Many independent problems evolved in one persistent launch (Sec. 2: tents of different
+ * meshes are trivially independent).  tents[n]: pitched tent lists of meshes with the same
+ * dimension and precision, any degrees 1..4 (default q = p + 1, m = 2p), any n_rhs each.
+ * Tents of all instances are taken in (layer, instance, vertex) order; each instance keeps its
+ * own dependency counters.  The batch refers to the tents handles: destroy it first. */
+int mtp_batch_create(int64_t n, const mtp_tents_t* tents, mtp_batch_t* out);
+void mtp_batch_destroy(mtp_batch_t batch);
+/* number of instances, total tents, total spacetime DOF count of one batch evolve */
+int mtp_batch_info(mtp_batch_t batch, int64_t* n_instances, int64_t* n_tents,
+                   double* spacetime_dofs);
+/* Evolve every instance i in place, states_dev[i] in its mesh's library layout, from t = 0 to
+ * the T its tents were pitched to.  Completion and errors as for mtp_evolve. */
+int mtp_batch_evolve(mtp_batch_t batch, void* const* states_dev, void* stream);
 
 /* Discrete adjoint of mtp_evolve (not in the paper): the reverse-in-time sweep through the
  * tent maps.  Given state0_dev (the state at t = 0) and lambda_T_dev = dJ/dY(T) for a

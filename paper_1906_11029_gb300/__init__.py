@@ -29,6 +29,7 @@ _CODES = {0: "MTP_OK", -1: "MTP_EINVAL", -2: "MTP_EMESH", -3: "MTP_ECAUSAL", -4:
 ABI_SYMBOLS = ["mtp_mesh_create", "mtp_mesh_destroy", "mtp_mesh_info", "mtp_pitch_tents",
                "mtp_tents_destroy", "mtp_tents_info", "mtp_tents_get", "mtp_state_from_lattice",
                "mtp_state_to_lattice", "mtp_evolve", "mtp_evolve_layers", "mtp_evolve_host",
+               "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_info", "mtp_batch_evolve",
                "mtp_adjoint", "mtp_energy", "mtp_energy_noalloc", "mtp_last_error"]
 
 
@@ -62,6 +63,10 @@ def _load():
         "mtp_evolve": (C.c_int, [P, P, D, P]),
         "mtp_evolve_layers": (C.c_int, [P, P, I64, I64, P]),
         "mtp_evolve_host": (C.c_int, [P, P, P, D, P]),
+        "mtp_batch_create": (C.c_int, [I64, P, C.POINTER(P)]),
+        "mtp_batch_destroy": (None, [P]),
+        "mtp_batch_info": (C.c_int, [P, P, P, P]),
+        "mtp_batch_evolve": (C.c_int, [P, P, P]),
         "mtp_adjoint": (C.c_int, [P, P, P, P, P, P, I64, P]),
         "mtp_energy": (C.c_int, [P, P, P, P]),
         "mtp_energy_noalloc": (C.c_int, [P, P, P, C.c_int, I64, C.c_int, C.c_int, C.c_int, P, P]),
@@ -176,6 +181,45 @@ def mtp_evolve_layers(tents, state_dev, layer_begin, layer_end, stream=None):
 
 def mtp_evolve_host(tents, state_in, state_out, T, stream=None):
     _check(_lib.mtp_evolve_host(tents, _ptr(state_in), _ptr(state_out), T, _stream(stream)))
+
+
+def mtp_batch_create(tents_handles):
+    arr = (C.c_void_p * len(tents_handles))(*[t.value if isinstance(t, C.c_void_p) else t for t in tents_handles])
+    h = C.c_void_p()
+    _check(_lib.mtp_batch_create(len(tents_handles), arr, C.byref(h)))
+    return h
+
+
+def mtp_batch_destroy(h):
+    _lib.mtp_batch_destroy(h)
+
+
+def mtp_batch_info(h):
+    ni, nt, st = C.c_int64(), C.c_int64(), C.c_double()
+    _check(_lib.mtp_batch_info(h, C.byref(ni), C.byref(nt), C.byref(st)))
+    return {"n_instances": ni.value, "n_tents": nt.value, "spacetime_dofs": st.value}
+
+
+def mtp_batch_evolve(h, states, stream=None):
+    arr = (C.c_void_p * len(states))(*[_ptr(s) for s in states])
+    _check(_lib.mtp_batch_evolve(h, arr, _stream(stream)))
+
+
+class Batch:
+    """Owns an mtp_batch_t over several Tents (kept alive here)."""
+
+    def __init__(self, tents_list):
+        self.tents = list(tents_list)
+        self.h = mtp_batch_create([t.h for t in self.tents])
+        self.info = mtp_batch_info(self.h)
+
+    def evolve(self, states, stream=None):
+        mtp_batch_evolve(self.h, states, stream)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            mtp_batch_destroy(self.h)
+            self.h = None
 
 
 def mtp_adjoint(tents, state0_dev, lam_T_dev, lam_0_dev, geps_dev, gmu_dev, checkpoint_every=0, stream=None):

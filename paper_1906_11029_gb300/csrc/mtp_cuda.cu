@@ -558,3 +558,108 @@ int device_adjoint(Tents& t, const void* state0, const void* lamT, void* lam0, d
 }
 
 }  // namespace mtp
+
+namespace mtp {
+
+struct DeviceBatch {
+    int32_t* ticket_inst = nullptr;
+    int64_t* ticket_tent = nullptr;
+    KArgs* kargs = nullptr;
+    PArgs* pargs = nullptr;
+    int32_t* inst_p = nullptr;
+    unsigned long long* next = nullptr;
+    int* err = nullptr;
+    int* err_host = nullptr;
+};
+
+void device_batch_free(Batch& b) {
+    if (!b.dev) return;
+    DeviceBatch& d = *b.dev;
+    void* ptrs[] = {d.ticket_inst, d.ticket_tent, d.kargs, d.pargs, d.inst_p, d.next, d.err};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (d.err_host) cudaFreeHost(d.err_host);
+    delete b.dev;
+    b.dev = nullptr;
+}
+
+int device_batch_evolve(Batch& b, void* const* states, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t ni = (int64_t)b.inst.size();
+    for (Tents* t : b.inst) MTP_TRY(device_tents_upload(*t));
+    const Mesh& m0 = *b.inst[0]->mesh;
+    static BatchEntry table[2][2];
+    static bool init = false;
+    if (!init) { batch_table(table); init = true; }
+    const BatchEntry& be = table[m0.precision == MTP_FP64 ? 0 : 1][m0.dim - 2];
+    if (!b.dev) {
+        b.dev = new DeviceBatch();
+        DeviceBatch& d = *b.dev;
+        MTP_TRY(upload(&d.ticket_inst, b.ticket_inst.data(), b.ticket_inst.size()));
+        MTP_TRY(upload(&d.ticket_tent, b.ticket_tent.data(), b.ticket_tent.size()));
+        std::vector<int32_t> ps(ni);
+        for (int64_t i = 0; i < ni; ++i) ps[i] = b.inst[i]->mesh->p;
+        MTP_TRY(upload(&d.inst_p, ps.data(), ps.size()));
+        CUDA_TRY(cudaMalloc((void**)&d.kargs, sizeof(KArgs) * ni));
+        CUDA_TRY(cudaMalloc((void**)&d.pargs, sizeof(PArgs) * ni));
+        CUDA_TRY(cudaMalloc((void**)&d.next, sizeof(unsigned long long)));
+        CUDA_TRY(cudaMalloc((void**)&d.err, sizeof(int)));
+        CUDA_TRY(cudaMallocHost((void**)&d.err_host, sizeof(int)));
+    }
+    DeviceBatch& d = *b.dev;
+    size_t smem = 0;
+    std::vector<KArgs> ka(ni);
+    std::vector<PArgs> pa(ni);
+    for (int64_t i = 0; i < ni; ++i) {
+        Tents& t = *b.inst[i];
+        Mesh& m = *t.mesh;
+        smem = std::max(smem, be.smem_bytes(m.p, m.max_patch));
+        fill_args(t, states[i], ka[i]);
+        ka[i].err = d.err;
+        DeviceTents& dt = *t.dev;
+        pa[i].n_tents = (int64_t)t.vertex.size();
+        pa[i].next = nullptr;
+        pa[i].cnt = dt.cnt;
+        pa[i].vt_ptr = dt.vt_ptr;
+        pa[i].vt_layer = dt.vt_layer;
+        pa[i].adj_ptr = dt.adj_ptr;
+        pa[i].adj = dt.adj;
+        pa[i].tent_layer = dt.tent_layer;
+        pa[i].timeout_ns = 10000000000LL;
+        pa[i].n_rhs = m.n_rhs;
+        CUDA_TRY(cudaMemsetAsync(dt.tau, 0, sizeof(double) * m.nv, st));   // flat front t = 0
+        CUDA_TRY(cudaMemsetAsync(dt.cnt, 0, sizeof(int) * m.nv, st));
+    }
+    int dev, smem_max, bpsm = 0, nsm = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if ((int64_t)smem > smem_max)
+        return set_error(MTP_EUNSUPPORTED, "batch kernel needs " + std::to_string(smem) +
+                                               " bytes of shared memory per block; the device allows " +
+                                               std::to_string(smem_max));
+    CUDA_TRY(be.prepare(smem, &bpsm));
+    CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaMemcpyAsync(d.kargs, ka.data(), sizeof(KArgs) * ni, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(d.pargs, pa.data(), sizeof(PArgs) * ni, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemsetAsync(d.next, 0, sizeof(unsigned long long), st));
+    CUDA_TRY(cudaMemsetAsync(d.err, 0, sizeof(int), st));
+    BatchArgs ba;
+    ba.n_tickets = (int64_t)b.ticket_inst.size();
+    ba.next = d.next;
+    ba.ticket_inst = d.ticket_inst;
+    ba.ticket_tent = d.ticket_tent;
+    ba.kargs = d.kargs;
+    ba.pargs = d.pargs;
+    ba.inst_p = d.inst_p;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ba.n_tickets, (int64_t)std::max(1, bpsm) * nsm));
+    CUDA_TRY(be.launch(ba, grid, smem, st));
+    CUDA_TRY(cudaMemcpyAsync(d.err_host, d.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));     // also keeps ka / pa alive until copied
+    if (*d.err_host == 1) return set_error(MTP_ECAUSAL, "a tent violated |grad phi| < sqrt(eps mu)");
+    if (*d.err_host == 2) return set_error(MTP_ENUMERIC, "non-finite value in the evolved state");
+    if (*d.err_host == 3) return set_error(MTP_ETIMEOUT, "a tent's wait for its predecessors exceeded the limit");
+    if (*d.err_host != 0) return set_error(MTP_ECUDA, "unknown device error word");
+    return MTP_OK;
+}
+
+}  // namespace mtp

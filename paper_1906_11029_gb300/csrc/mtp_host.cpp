@@ -432,6 +432,7 @@ using namespace mtp;
 
 struct mtp_mesh { Mesh m; };
 struct mtp_tents { Tents t; };
+struct mtp_batch { Batch b; };
 
 #define MTP_GUARD_BEGIN try {
 #define MTP_GUARD_END                                                        \
@@ -571,6 +572,68 @@ int mtp_adjoint(mtp_tents_t tents, const void* state0, const void* lamT, void* l
     if (!tents || !state0 || !lamT || !lam0 || !geps || !gmu) return set_error(MTP_EINVAL, "NULL argument");
     if (checkpoint_every < 0) return set_error(MTP_EINVAL, "checkpoint_every must be >= 0");
     return device_adjoint(tents->t, state0, lamT, lam0, geps, gmu, checkpoint_every, stream);
+    MTP_GUARD_END
+}
+
+int mtp_batch_create(int64_t n, const mtp_tents_t* tents, mtp_batch_t* out) {
+    MTP_GUARD_BEGIN
+    if (!out) return set_error(MTP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !tents) return set_error(MTP_EINVAL, "need at least one instance");
+    auto h = std::make_unique<mtp_batch>();
+    for (int64_t i = 0; i < n; ++i) {
+        if (!tents[i]) return set_error(MTP_EINVAL, "NULL tents handle in the batch");
+        const Mesh& m = *tents[i]->t.mesh;
+        const Mesh& m0 = *tents[0]->t.mesh;
+        if (m.dim != m0.dim || m.precision != m0.precision)
+            return set_error(MTP_EINVAL, "all instances of a batch need the same dimension and precision");
+        if (m.q != m.p + 1 || m.m != 2 * m.p)
+            return set_error(MTP_EUNSUPPORTED, "batched instances use the default q = p + 1, m = 2p");
+        h->b.inst.push_back(&tents[i]->t);
+        h->b.spacetime_dofs += tents[i]->t.spacetime_dofs;
+    }
+    // tickets: all tents ordered by (layer, instance, vertex)
+    int64_t nt = 0, nl = 0;
+    for (Tents* t : h->b.inst) {
+        nt += (int64_t)t->vertex.size();
+        nl = std::max<int64_t>(nl, (int64_t)t->layer_ptr.size() - 1);
+    }
+    h->b.ticket_inst.reserve(nt);
+    h->b.ticket_tent.reserve(nt);
+    for (int64_t l = 0; l < nl; ++l)
+        for (int64_t i = 0; i < n; ++i) {
+            const Tents& t = *h->b.inst[i];
+            if (l + 1 >= (int64_t)t.layer_ptr.size()) continue;
+            for (int64_t q = t.layer_ptr[l]; q < t.layer_ptr[l + 1]; ++q) {
+                h->b.ticket_inst.push_back((int32_t)i);
+                h->b.ticket_tent.push_back(q);
+            }
+        }
+    *out = h.release();
+    return MTP_OK;
+    MTP_GUARD_END
+}
+
+void mtp_batch_destroy(mtp_batch_t batch) {
+    if (!batch) return;
+    device_batch_free(batch->b);
+    delete batch;
+}
+
+int mtp_batch_info(mtp_batch_t batch, int64_t* n_instances, int64_t* n_tents, double* spacetime_dofs) {
+    if (!batch) return set_error(MTP_EINVAL, "batch is NULL");
+    if (n_instances) *n_instances = (int64_t)batch->b.inst.size();
+    if (n_tents) *n_tents = (int64_t)batch->b.ticket_inst.size();
+    if (spacetime_dofs) *spacetime_dofs = batch->b.spacetime_dofs;
+    return MTP_OK;
+}
+
+int mtp_batch_evolve(mtp_batch_t batch, void* const* states, void* stream) {
+    MTP_GUARD_BEGIN
+    if (!batch || !states) return set_error(MTP_EINVAL, "NULL argument");
+    for (size_t i = 0; i < batch->b.inst.size(); ++i)
+        if (!states[i]) return set_error(MTP_EINVAL, "NULL state for instance " + std::to_string(i));
+    return device_batch_evolve(batch->b, states, stream);
     MTP_GUARD_END
 }
 

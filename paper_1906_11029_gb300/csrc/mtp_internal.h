@@ -75,6 +75,14 @@ struct Tents {
     struct DeviceTents* dev = nullptr;
 };
 
+struct Batch {
+    std::vector<Tents*> inst;
+    std::vector<int32_t> ticket_inst;
+    std::vector<int64_t> ticket_tent;
+    double spacetime_dofs = 0;
+    struct DeviceBatch* dev = nullptr;
+};
+
 // error reporting
 int set_error(int code, const std::string& msg);
 
@@ -91,6 +99,8 @@ int device_evolve(Tents& t, void* state, int64_t layer_begin, int64_t layer_end,
                   void* stream);
 int device_evolve_host(Tents& t, const void* in, void* out, void* stream);
 int device_energy(Mesh& m, const void* state, double* out_host, void* stream);
+int device_batch_evolve(Batch& b, void* const* states, void* stream);
+void device_batch_free(Batch& b);
 int device_adjoint(Tents& t, const void* state0, const void* lamT, void* lam0, double* geps, double* gmu,
                    int64_t checkpoint_every, void* stream);
 

@@ -715,16 +715,71 @@ __device__ __forceinline__ long long globaltimer() {
     return t;
 }
 
+// One DAG-walk step for ticket `tent` of an instance: bounded wait on the closed neighbourhood,
+// all right-hand sides, publish.  Returns false when the CTA must stop (error / timeout).
 template <typename Real, int DIM, int P>
-__global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::value) tent_persistent_kernel(const KArgs a, const PArgs pa) {
+__device__ bool tent_dag_step(unsigned char* smem, const KArgs& a, const PArgs& pa, int64_t tent, int* s_abort) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NT = Sh::NT, NBP = Sh::NBP, ESZ = NF * NBP;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ long long s_ticket;
-    __shared__ int s_abort;
     const SmemLayout<Real, DIM, P> lay(a.max_patch);
     TentCtx<Real, DIM, P> c;
     c.carve(smem, lay);
+    const int V = a.tent_v[tent];
+    const int L = pa.tent_layer[tent];
+    const int64_t a0 = pa.adj_ptr[V], deg = pa.adj_ptr[V + 1] - a0;
+    for (int u = threadIdx.x; u <= deg; u += NT) {
+        const int U = u == 0 ? V : pa.adj[a0 + u - 1];
+        int64_t lo = pa.vt_ptr[U], hi = pa.vt_ptr[U + 1];
+        const int64_t base = lo;
+        while (lo < hi) {                      // first tent of U with layer >= L
+            const int64_t mid = (lo + hi) / 2;
+            if (pa.vt_layer[mid] < L) lo = mid + 1; else hi = mid;
+        }
+        const int need = (int)(lo - base);
+        if (load_acquire(pa.cnt + U) < need) {
+            const long long deadline = globaltimer() + pa.timeout_ns;
+            while (load_acquire(pa.cnt + U) < need) {
+                if (*(volatile int*)a.err != 0 || globaltimer() > deadline) {
+                    atomicCAS(a.err, 0, 3);
+                    *s_abort = 1;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+    }
+    __syncthreads();
+    if (*s_abort) return false;
+    for (int r = 0; r < pa.n_rhs; ++r) {
+        Real* state = (Real*)a.state + (int64_t)r * a.rhs_stride;
+        tent_setup<Real, DIM, P, true>(c, a, tent, state);
+        tent_sat(c, a, (Real*)nullptr);
+        bool bad = false;
+        for (int idx = threadIdx.x; idx < c.ns * NF * NB; idx += NT) {
+            const int k = idx / (NF * NB), rr = idx - k * NF * NB, s = rr / NB, b = rr - s * NB;
+            const Real v = c.sY[k * ESZ + s * NBP + b];
+            if (!isfinite((double)v)) bad = true;
+            state[(int64_t)a.patch_elem[c.pb + k] * NF * NB + rr] = v;
+        }
+        if (bad) atomicExch(a.err, 2);
+        __threadfence();                       // publish this thread's state writes (gpu scope)
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.tau[V] = a.tent_tt[tent];
+        __threadfence();
+        atomicAdd(pa.cnt + V, 1);
+    }
+    __syncthreads();
+    return true;
+}
+
+template <typename Real, int DIM, int P>
+__global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::value)
+    tent_persistent_kernel(const KArgs a, const PArgs pa) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_ticket;
+    __shared__ int s_abort;
     while (true) {
         if (threadIdx.x == 0) {
             s_ticket = (long long)atomicAdd(pa.next, 1ull);
@@ -733,54 +788,49 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::va
         __syncthreads();
         const long long tent = s_ticket;
         if (tent >= pa.n_tents) break;
-        // wait for the closed neighbourhood of V (one thread per vertex)
-        const int V = a.tent_v[tent];
-        const int L = pa.tent_layer[tent];
-        const int64_t a0 = pa.adj_ptr[V], deg = pa.adj_ptr[V + 1] - a0;
-        for (int u = threadIdx.x; u <= deg; u += NT) {
-            const int U = u == 0 ? V : pa.adj[a0 + u - 1];
-            int64_t lo = pa.vt_ptr[U], hi = pa.vt_ptr[U + 1];
-            const int64_t base = lo;
-            while (lo < hi) {                      // first tent of U with layer >= L
-                const int64_t mid = (lo + hi) / 2;
-                if (pa.vt_layer[mid] < L) lo = mid + 1; else hi = mid;
-            }
-            const int need = (int)(lo - base);
-            if (load_acquire(pa.cnt + U) < need) {
-                const long long deadline = globaltimer() + pa.timeout_ns;
-                while (load_acquire(pa.cnt + U) < need) {
-                    if (*(volatile int*)a.err != 0 || globaltimer() > deadline) {
-                        atomicCAS(a.err, 0, 3);
-                        s_abort = 1;
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-        }
-        __syncthreads();
-        if (s_abort) break;
-        for (int r = 0; r < pa.n_rhs; ++r) {
-            Real* state = (Real*)a.state + (int64_t)r * a.rhs_stride;
-            tent_setup<Real, DIM, P, true>(c, a, tent, state);
-            tent_sat(c, a, (Real*)nullptr);
-            bool bad = false;
-            for (int idx = threadIdx.x; idx < c.ns * NF * NB; idx += NT) {
-                const int k = idx / (NF * NB), rr = idx - k * NF * NB, s = rr / NB, b = rr - s * NB;
-                const Real v = c.sY[k * ESZ + s * NBP + b];
-                if (!isfinite((double)v)) bad = true;
-                state[(int64_t)a.patch_elem[c.pb + k] * NF * NB + rr] = v;
-            }
-            if (bad) atomicExch(a.err, 2);
-            __threadfence();                       // publish this thread's state writes (gpu scope)
-            __syncthreads();
-        }
+        if (!tent_dag_step<Real, DIM, P>(smem, a, pa, tent, &s_abort)) break;
+    }
+}
+
+// Many independent problems (meshes of any degree 1..4, same dimension and precision) in one
+// persistent launch: tickets run over the merged tent lists ordered by (layer, instance,
+// vertex); each ticket names its instance, whose KArgs / PArgs (own counters) live in global
+// memory.  Instances never wait on each other.
+struct BatchArgs {
+    int64_t n_tickets;
+    unsigned long long* next;
+    const int32_t* ticket_inst;
+    const int64_t* ticket_tent;
+    const KArgs* kargs;
+    const PArgs* pargs;
+    const int32_t* inst_p;
+};
+
+template <typename Real, int DIM>
+__global__ void __launch_bounds__(Shape<DIM, 4>::NT, sizeof(Real) == 4 ? 2 : 1) tent_batch_kernel(const BatchArgs b) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long s_ticket;
+    __shared__ int s_abort;
+    while (true) {
         if (threadIdx.x == 0) {
-            a.tau[V] = a.tent_tt[tent];
-            __threadfence();
-            atomicAdd(pa.cnt + V, 1);
+            s_ticket = (long long)atomicAdd(b.next, 1ull);
+            s_abort = 0;
         }
         __syncthreads();
+        const long long t = s_ticket;
+        if (t >= b.n_tickets) break;
+        const int inst = b.ticket_inst[t];
+        const int64_t tent = b.ticket_tent[t];
+        const KArgs& a = b.kargs[inst];      // per-instance arguments stay in global memory
+        const PArgs& pa = b.pargs[inst];
+        bool ok = true;
+        switch (b.inst_p[inst]) {
+            case 1: ok = tent_dag_step<Real, DIM, 1>(smem, a, pa, tent, &s_abort); break;
+            case 2: ok = tent_dag_step<Real, DIM, 2>(smem, a, pa, tent, &s_abort); break;
+            case 3: ok = tent_dag_step<Real, DIM, 3>(smem, a, pa, tent, &s_abort); break;
+            default: ok = tent_dag_step<Real, DIM, 4>(smem, a, pa, tent, &s_abort); break;
+        }
+        if (!ok) break;
     }
 }
 

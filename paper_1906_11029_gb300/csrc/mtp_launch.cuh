@@ -66,6 +66,17 @@ struct AdjEntry {
 // entries[precision][dim - 2][p - 1]
 void adjoint_table(AdjEntry entries[2][2][4]);
 
+using BatchLaunchFn = cudaError_t (*)(const BatchArgs&, int grid, size_t smem, cudaStream_t st);
+using BatchPrepFn = cudaError_t (*)(size_t smem, int* blocks_per_sm);
+using BatchSmemFn = size_t (*)(int p, int max_patch);
+struct BatchEntry {
+    BatchLaunchFn launch;
+    BatchPrepFn prepare;
+    BatchSmemFn smem_bytes;
+};
+// entries[precision][dim - 2]
+void batch_table(BatchEntry entries[2][2]);
+
 #define MTP_KERNEL_TABLE(NAME, REAL)                                                   \
     void NAME(KernelEntry e[2][4]) {                                                   \
         e[0][0] = {launch_tent_kernel<REAL, 2, 1>, prepare_tent_kernel<REAL, 2, 1>, \
