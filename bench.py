@@ -37,7 +37,7 @@ N_SMS = 152
 # the current kernel version (profiles/tent_layer_kernel_fp32_p4_graded32.md); None once the
 # kernel has changed since the counters were taken.
 TRAFFIC_BYTES_PER_TENT = {"fp32": 27526.0}          # tent_layer_kernel, per tent
-TRAFFIC_PERSISTENT_BYTES = {}                         # tent_persistent_kernel, per tent (not captured yet)
+TRAFFIC_PERSISTENT_BYTES = {"fp32": 24425.0}          # tent_persistent_kernel, per tent (full evolve)
 
 
 def load_peaks():
@@ -218,6 +218,52 @@ def run_profile_evolve(args):
     print(json.dumps({"profile_evolve": w.name, "tents": tents.info["n_tents"]}))
 
 
+def run_many(args):
+    """Many-instance workload: 64 independent PEC cube problems, n ~ U{6..20}, p ~ U{2,3,4}
+    (seed 4), 4 Gaussian-pulse right-hand sides each, FP32, T = 0.5, one persistent launch."""
+    import torch
+    import mtp_synth as S
+    import paper_1906_11029_gb300 as mtp
+    recipe = S.many_instances(args.many_count, seed=4, n_rhs=4)
+    insts = []
+    t0 = time.perf_counter()
+    for r in recipe:
+        v, e = S.cube_mesh(r["n"])
+        one = np.ones(len(e))
+        m = mtp.Mesh(3, v, e, one, one, p=r["p"], precision=mtp.MTP_FP32, n_rhs=4)
+        t = m.pitch(r["T"], 0.5)
+        pts = S.lattice_points(v, e, r["p"])
+        vals = np.stack([np.concatenate(S.gaussian_pulse(c, r["width"])(pts), -1) for c in r["centres"]])
+        st = m.state_from_lattice(torch.tensor(np.ascontiguousarray(vals), device="cuda"))
+        del vals, pts
+        insts.append((m, t, st))
+    batch = mtp.Batch([t for _, t, _ in insts])
+    setup_s = time.perf_counter() - t0
+    dofs = batch.info["spacetime_dofs"]
+    for _ in range(args.warmup):
+        batch.evolve([st.clone() for _, _, st in insts])
+    torch.cuda.synchronize()
+    work = [st.clone() for _, _, st in insts]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    for _ in range(args.steps):
+        for wk, (_, _, st) in zip(work, insts):
+            wk.copy_(st)
+        a.record()
+        batch.evolve(work)
+        b.record()
+        torch.cuda.synchronize()
+        ms += a.elapsed_time(b)
+    print(json.dumps({"metric": "spacetime DOF-updates/s", "value": args.steps * dofs / (ms / 1e3),
+                      "unit": "DOF-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms / args.steps, "higher_is_better": True, "dtype": "f32",
+                      "data": "synthetic", "gpu_launches": args.steps,
+                      "config": {"workload": f"many_instances_{args.many_count}x4rhs",
+                                 "tents": batch.info["n_tents"], "dof_updates_per_step": dofs,
+                                 "elems_total": int(sum(m.info["n_elems"] for m, _, _ in insts)),
+                                 "setup_s": setup_s}}))
+
+
 def run_mtp(args):
     import torch
     import paper_1906_11029_gb300 as mtp
@@ -384,7 +430,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mtp", choices=["mtp", "reference"])
-    ap.add_argument("--workload", default="graded", choices=["graded", "cube", "small"])
+    ap.add_argument("--workload", default="graded", choices=["graded", "cube", "small", "many"])
+    ap.add_argument("--many-count", type=int, default=64)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--fp64-window", type=float, default=0.02)
     ap.add_argument("--layer-launches", action="store_true", help="one launch per layer instead of the DAG walk")
@@ -406,6 +453,8 @@ def main():
         return run_profile(args)
     if args.profile_evolve:
         return run_profile_evolve(args)
+    if args.workload == "many":
+        return run_many(args)
     return run_mtp(args)
 
 
