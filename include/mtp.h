@@ -19,7 +19,7 @@
  *     unless stated otherwise.
  *   - State layout ("library layout"): state[r][e][f][a], r < n_rhs, e < n_elems,
  *     f < n_fields, a < n_basis, in the mesh's precision (double for MTP_FP64, float
- *     for MTP_FP32).  The coefficients are those of the conserved variable
+ *     for the others).  The coefficients are those of the conserved variable
  *     y = g(u) - f(u) grad(phi) (Sec. 3, transformed equation; y = (eps E, mu H) on
  *     a flat front) in an L2-orthonormal basis of P_p on each element.
  *   - Lattice layout: vals[r][e][k][f] in double, the value of y at lattice point k
@@ -54,8 +54,12 @@ extern "C" {
                                        persistent DAG-walking kernel */
 
 /* precision of the state and of the operator arithmetic */
-#define MTP_FP64 0
-#define MTP_FP32 1
+#define MTP_FP64   0   /* FP64 state and arithmetic */
+#define MTP_FP32   1   /* FP32 state and arithmetic (geometry and G^-1 built in FP64) */
+#define MTP_TF32   2   /* 3D: FP32 state; traces, volume and lift contractions on tensor cores
+                          with TF32 operands and FP32 accumulation */
+#define MTP_TF32X3 3   /* 3D: as MTP_TF32 with each operand split into TF32 hi + lo parts and
+                          three products (hi*hi + hi*lo + lo*hi), about FP32 accuracy */
 
 typedef struct mtp_mesh*  mtp_mesh_t;
 typedef struct mtp_tents* mtp_tents_t;
@@ -65,7 +69,7 @@ typedef struct {
     int p;          /* polynomial degree of V_h, 1..4 (Sec. 3, DG space)                   */
     int q;          /* SAT stages; 0 selects p+1 (Sec. 5.1)                                */
     int m;          /* SAT sub-intervals per tent; 0 selects 2p (Sec. 5.1)                 */
-    int precision;  /* MTP_FP64 or MTP_FP32                                                */
+    int precision;  /* MTP_FP64, MTP_FP32, MTP_TF32 or MTP_TF32X3                            */
     int n_rhs;      /* independent states evolved with the same tents (>= 1; 0 means 1)   */
     int flags;      /* MTP_FLAG_* bits; 0 by default                                       */
 } mtp_options;
@@ -198,6 +202,12 @@ int mtp_energy(mtp_mesh_t mesh, const void* state_dev, double* out_host, void* s
 int mtp_energy_noalloc(const void* state_dev, const double* eps_dev, const double* mu_dev,
                        int dim, int64_t n_elems, int p, int precision, int n_rhs,
                        double* out_dev, void* stream);
+
+/* Measured arithmetic rates of the current device, in TFLOP/s (roofline denominators that the
+ * host cannot look up): out_tflops[0] FP32 FMA, [1] FP64 FMA, [2] warp-level tensor-core MMA
+ * TF32 (m16n8k8, FP32 accumulate), [3] warp-level MMA BF16 (m16n8k16, FP32 accumulate).
+ * Synchronises the stream; allocates a small scratch buffer. */
+int mtp_probe_rates(double* out_tflops, void* stream);
 
 /* Thread-local description of the last error returned on this thread. */
 const char* mtp_last_error(void);

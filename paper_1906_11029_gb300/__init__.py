@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libmtp.so")
 
 MTP_OK, MTP_EINVAL, MTP_EMESH, MTP_ECAUSAL = 0, -1, -2, -3
 MTP_ENOMEM, MTP_ECUDA, MTP_ETIMEOUT, MTP_ENUMERIC, MTP_EUNSUPPORTED = -4, -5, -6, -7, -8
-MTP_FP64, MTP_FP32 = 0, 1
+MTP_FP64, MTP_FP32, MTP_TF32, MTP_TF32X3 = 0, 1, 2, 3
 MTP_FLAG_LAYER_LAUNCHES = 1
 _CODES = {0: "MTP_OK", -1: "MTP_EINVAL", -2: "MTP_EMESH", -3: "MTP_ECAUSAL", -4: "MTP_ENOMEM",
           -5: "MTP_ECUDA", -6: "MTP_ETIMEOUT", -7: "MTP_ENUMERIC", -8: "MTP_EUNSUPPORTED"}
@@ -30,7 +30,7 @@ ABI_SYMBOLS = ["mtp_mesh_create", "mtp_mesh_destroy", "mtp_mesh_info", "mtp_pitc
                "mtp_tents_destroy", "mtp_tents_info", "mtp_tents_get", "mtp_state_from_lattice",
                "mtp_state_to_lattice", "mtp_evolve", "mtp_evolve_layers", "mtp_evolve_host",
                "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_info", "mtp_batch_evolve",
-               "mtp_adjoint", "mtp_energy", "mtp_energy_noalloc", "mtp_last_error"]
+               "mtp_adjoint", "mtp_energy", "mtp_energy_noalloc", "mtp_probe_rates", "mtp_last_error"]
 
 
 class MtpError(RuntimeError):
@@ -70,6 +70,7 @@ def _load():
         "mtp_adjoint": (C.c_int, [P, P, P, P, P, P, I64, P]),
         "mtp_energy": (C.c_int, [P, P, P, P]),
         "mtp_energy_noalloc": (C.c_int, [P, P, P, C.c_int, I64, C.c_int, C.c_int, C.c_int, P, P]),
+        "mtp_probe_rates": (C.c_int, [P, P]),
         "mtp_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -237,6 +238,13 @@ def mtp_energy_noalloc(state_dev, eps_dev, mu_dev, dim, n_elems, p, precision, n
     """Energies into the caller's device buffer out_dev[n_rhs]; allocates nothing (see mtp.h)."""
     _check(_lib.mtp_energy_noalloc(_ptr(state_dev), _ptr(eps_dev), _ptr(mu_dev), dim, n_elems, p, precision,
                                    n_rhs, _ptr(out_dev), _stream(stream)))
+
+
+def mtp_probe_rates(stream=None):
+    """{"fp32_fma", "fp64_fma", "mma_tf32", "mma_bf16"} in TFLOP/s, measured on the current device."""
+    out = np.zeros(4, np.float64)
+    _check(_lib.mtp_probe_rates(_ptr(out), _stream(stream)))
+    return dict(zip(["fp32_fma", "fp64_fma", "mma_tf32", "mma_bf16"], out.tolist()))
 
 
 # ------------------------------------------------------------------------ convenience wrappers

@@ -33,6 +33,12 @@ struct DeviceMesh {
     void* L = nullptr;
     double* V = nullptr;
     double* Vinv = nullptr;
+    float* Sf = nullptr;          // tensor-core fragment tables (TF32 modes)
+    float* Lfr = nullptr;
+    float* Trf = nullptr;
+    float* Sf_lo = nullptr;
+    float* Lfr_lo = nullptr;
+    float* Trf_lo = nullptr;
     double* partial = nullptr;    // energy reduction scratch: [n_rhs][kEnergyBlocks] partials, then [n_rhs] sums
 };
 
@@ -95,6 +101,35 @@ static int upload_real(const Mesh& m, void** dst, const std::vector<double>& src
         if (_rc != MTP_OK) return _rc; \
     } while (0)
 
+// A-operand tables in m16n8k8 fragment order: fragment (mt, kt) of a row-major M x K matrix
+// A (zero outside rows < rows, cols < cols) is 32 lanes x 4 values: lane (g = lane/4,
+// t = lane%4) holds A[16mt+g][8kt+t], A[16mt+g+8][8kt+t], A[16mt+g][8kt+t+4], A[16mt+g+8][8kt+t+4].
+// Values are TF32-rounded (round to nearest even at 10 mantissa bits); `lo` receives the
+// TF32-rounded remainder for the split mode.
+static float tf32_round(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) != 0x7f800000u) u += 0xfffu + ((u >> 13) & 1u);
+    u &= 0xffffe000u;
+    std::memcpy(&x, &u, 4);
+    return x;
+}
+template <typename Get>
+static void append_fragments(std::vector<float>& hi, std::vector<float>& lo, int MT, int KT, Get A) {
+    for (int mt = 0; mt < MT; ++mt)
+        for (int kt = 0; kt < KT; ++kt)
+            for (int lane = 0; lane < 32; ++lane) {
+                const int g = lane >> 2, t = lane & 3;
+                const double v[4] = {A(16 * mt + g, 8 * kt + t), A(16 * mt + g + 8, 8 * kt + t),
+                                     A(16 * mt + g, 8 * kt + t + 4), A(16 * mt + g + 8, 8 * kt + t + 4)};
+                for (int q = 0; q < 4; ++q) {
+                    const float h = tf32_round((float)v[q]);
+                    hi.push_back(h);
+                    lo.push_back(tf32_round((float)(v[q] - (double)h)));
+                }
+            }
+}
+
 int device_mesh_upload(Mesh& m) {
     int dev;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -113,6 +148,32 @@ int device_mesh_upload(Mesh& m) {
     MTP_TRY(upload_real(m, &d.S, pad_rows(m.ref.S, m.nb)));     // [j][l][a][NBP]
     MTP_TRY(upload_real(m, &d.Tr, pad_rows(m.ref.Tr, m.nb)));   // [f][c][NBP]
     MTP_TRY(upload_real(m, &d.L, pad_rows(m.ref.L, m.nfb)));    // [j][f][a][NFBP]
+    if (m.precision == MTP_TF32 || m.precision == MTP_TF32X3) {
+        const RefTables& r = m.ref;
+        const int nb = m.nb, nfb = m.nfb, d3 = m.dim, nvx = m.dim + 1;
+        const int MT = (nb + 15) / 16, KT = (nb + 7) / 8, KTL = (nfb + 7) / 8;
+        std::vector<float> sh, sl, lh, ll, th, tl;
+        for (int j = 0; j <= d3; ++j)
+            for (int l = 0; l < d3; ++l)
+                append_fragments(sh, sl, MT, KT, [&](int a, int b) {
+                    return (a < nb && b < nb) ? r.S[(((size_t)j * d3 + l) * nb + a) * nb + b] : 0.0;
+                });
+        for (int j = 0; j <= d3; ++j)
+            for (int f = 0; f < nvx; ++f)
+                append_fragments(lh, ll, MT, KTL, [&](int a, int cc) {
+                    return (a < nb && cc < nfb) ? r.L[(((size_t)j * nvx + f) * nb + a) * nfb + cc] : 0.0;
+                });
+        for (int f = 0; f < nvx; ++f)
+            append_fragments(th, tl, 1, KT, [&](int cc, int b) {
+                return (cc < nfb && b < nb) ? r.Tr[((size_t)f * nfb + cc) * nb + b] : 0.0;
+            });
+        MTP_TRY(upload(&d.Sf, sh.data(), sh.size()));
+        MTP_TRY(upload(&d.Lfr, lh.data(), lh.size()));
+        MTP_TRY(upload(&d.Trf, th.data(), th.size()));
+        MTP_TRY(upload(&d.Sf_lo, sl.data(), sl.size()));
+        MTP_TRY(upload(&d.Lfr_lo, ll.data(), ll.size()));
+        MTP_TRY(upload(&d.Trf_lo, tl.data(), tl.size()));
+    }
     MTP_TRY(upload(&d.V, m.ref.V.data(), m.ref.V.size()));
     MTP_TRY(upload(&d.Vinv, m.ref.Vinv.data(), m.ref.Vinv.size()));
     CUDA_TRY(cudaMalloc((void**)&d.partial, sizeof(double) * (kEnergyBlocks + 1) * m.n_rhs));
@@ -122,7 +183,8 @@ int device_mesh_upload(Mesh& m) {
 void device_mesh_free(Mesh& m) {
     if (!m.dev) return;
     DeviceMesh& d = *m.dev;
-    void* ptrs[] = {d.geo, d.elems, d.patch_ptr, d.patch_elem, d.patch_info, d.S, d.Tr, d.L, d.V, d.Vinv, d.partial};
+    void* ptrs[] = {d.geo, d.elems, d.patch_ptr, d.patch_elem, d.patch_info, d.S, d.Tr, d.L, d.V, d.Vinv, d.partial,
+                    d.Sf, d.Lfr, d.Trf, d.Sf_lo, d.Lfr_lo, d.Trf_lo};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m.dev;
@@ -176,15 +238,19 @@ static int device_tents_upload(Tents& t) {
 }
 
 static const KernelEntry& kernel_entry(const Mesh& m) {
-    static KernelEntry f64[2][4], f32[2][4];
+    static KernelEntry f64[2][4], f32[2][4], tc[2][4];
     static bool init = false;
     if (!init) {
         kernel_table_f64(f64);
         kernel_table_f32(f32);
+        kernel_table_tc(tc);
         init = true;
     }
+    if (m.precision == MTP_TF32 || m.precision == MTP_TF32X3)
+        return tc[m.precision == MTP_TF32 ? 0 : 1][m.p - 1];
     return (m.precision == MTP_FP64 ? f64 : f32)[m.dim - 2][m.p - 1];
 }
+
 
 // ---------------------------------------------------------------------------------
 // lattice exchange: y(x_k) = (1/sqrt|det J|) sum_a V[k][a] Y_a and its inverse
@@ -340,6 +406,12 @@ static void fill_args(Tents& t, void* state, KArgs& a) {
     a.S = dm.S;
     a.Tr = dm.Tr;
     a.L = dm.L;
+    a.Sf = (const float4*)dm.Sf;
+    a.Lfr = (const float4*)dm.Lfr;
+    a.Trf = (const float4*)dm.Trf;
+    a.Sf_lo = (const float4*)dm.Sf_lo;
+    a.Lfr_lo = (const float4*)dm.Lfr_lo;
+    a.Trf_lo = (const float4*)dm.Trf_lo;
     a.state = state;
     a.rhs_stride = m.ne * m.nf * m.nb;
     a.err = dt.err;
@@ -591,6 +663,8 @@ int device_batch_evolve(Batch& b, void* const* states, void* stream) {
     static BatchEntry table[2][2];
     static bool init = false;
     if (!init) { batch_table(table); init = true; }
+    if (m0.precision == MTP_TF32 || m0.precision == MTP_TF32X3)
+        return set_error(MTP_EUNSUPPORTED, "batches run FP64 or FP32 SIMT meshes; tensor-core modes are per mesh");
     const BatchEntry& be = table[m0.precision == MTP_FP64 ? 0 : 1][m0.dim - 2];
     if (!b.dev) {
         b.dev = new DeviceBatch();

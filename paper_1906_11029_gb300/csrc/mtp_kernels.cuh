@@ -47,6 +47,14 @@ struct KArgs {
     const void* S;              // [j][l][a][NBP]  reference tables in the state precision,
     const void* Tr;             // [f][c][NBP]     rows padded with zeros (see pad4)
     const void* L;              // [j][f][a][NFBP]
+    // tensor-core modes: A-operand tables in m16n8k8 fragment order (32 lanes x 4 TF32 values
+    // per fragment), hi part and (split mode) lo part
+    const float4* Sf;           // [j][l][mt][kt]
+    const float4* Lfr;          // [j][f][mt][ktl]
+    const float4* Trf;          // [f][kt]
+    const float4* Sf_lo;
+    const float4* Lfr_lo;
+    const float4* Trf_lo;
     void* state;                // [rhs][ne][nf][nb]
     int64_t rhs_stride;         // ne * nf * nb
     int* err;                   // error word (0 = ok, 1 = causality, 2 = non-finite)
@@ -635,7 +643,15 @@ __device__ void tent_copy(int ns, const Real* src, Real* dst) {
 
 // All m x q SAT stages of one tent on the shared-memory state sY.  With a tape, Y_{i,0}
 // goes to slot i and U_{i,n} to slot m + i q + n (each slot max_patch x ESZ entries).
-template <typename Real, int DIM, int P>
+template <typename Real, int DIM, int P, int MODE>
+__device__ void tent_traces_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real* Ucur, Real* tr);
+template <typename Real, int DIM, int P, int MODE>
+__device__ void tent_stage_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, const Real* Ucur, Real* Unext,
+                              const Real* tr);
+
+// MODE 0: SIMT contractions in the state precision; 1: TF32 tensor-core MMAs (FP32 state,
+// FP32 accumulate); 2: the same with a 3-term hi + lo split of both operands.
+template <typename Real, int DIM, int P, int MODE = 0>
 __device__ void tent_sat(TentCtx<Real, DIM, P>& c, const KArgs& a, Real* tape) {
     constexpr int ESZ = Shape<DIM, P>::NF * Shape<DIM, P>::NBP;
     const size_t slot = (size_t)a.max_patch * ESZ;
@@ -649,18 +665,20 @@ __device__ void tent_sat(TentCtx<Real, DIM, P>& c, const KArgs& a, Real* tape) {
         __syncthreads();
         for (int n = 1; n <= a.q; ++n) {
             if (tape) tent_copy<Real, DIM, P>(c.ns, Ucur, tape + (size_t)(a.m + i * a.q + n - 1) * slot);
-            tent_traces(c, a, Ucur, c.sTr);
+            if constexpr (MODE == 0) tent_traces(c, a, Ucur, c.sTr);
+            else tent_traces_tc<Real, DIM, P, MODE>(c, a, Ucur, c.sTr);
             __syncthreads();
             tent_fluxes(c, c.sTr);
             __syncthreads();
-            tent_stage(c, a, n, Ucur, Unext, c.sTr);
+            if constexpr (MODE == 0) tent_stage(c, a, n, Ucur, Unext, c.sTr);
+            else tent_stage_tc<Real, DIM, P, MODE>(c, a, n, Ucur, Unext, c.sTr);
             __syncthreads();
             Real* tmp = Ucur; Ucur = Unext; Unext = tmp;
         }
     }
 }
 
-template <typename Real, int DIM, int P>
+template <typename Real, int DIM, int P, int MODE = 0>
 __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::value) tent_layer_kernel(const KArgs a, int64_t t0) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NT = Sh::NT, NBP = Sh::NBP, ESZ = NF * NBP;
@@ -671,7 +689,7 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::va
     const int64_t tent = t0 + blockIdx.x;
     Real* state = (Real*)a.state + (int64_t)blockIdx.y * a.rhs_stride;
     tent_setup(c, a, tent, state);
-    tent_sat(c, a, (Real*)nullptr);
+    tent_sat<Real, DIM, P, MODE>(c, a, (Real*)nullptr);
     // ---- (d) scatter the tent-top Y; advance the front at V ----
     bool bad = false;
     for (int idx = threadIdx.x; idx < c.ns * NF * NB; idx += NT) {
@@ -717,7 +735,7 @@ __device__ __forceinline__ long long globaltimer() {
 
 // One DAG-walk step for ticket `tent` of an instance: bounded wait on the closed neighbourhood,
 // all right-hand sides, publish.  Returns false when the CTA must stop (error / timeout).
-template <typename Real, int DIM, int P>
+template <typename Real, int DIM, int P, int MODE = 0>
 __device__ bool tent_dag_step(unsigned char* smem, const KArgs& a, const PArgs& pa, int64_t tent, int* s_abort) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NT = Sh::NT, NBP = Sh::NBP, ESZ = NF * NBP;
@@ -753,7 +771,7 @@ __device__ bool tent_dag_step(unsigned char* smem, const KArgs& a, const PArgs& 
     for (int r = 0; r < pa.n_rhs; ++r) {
         Real* state = (Real*)a.state + (int64_t)r * a.rhs_stride;
         tent_setup<Real, DIM, P, true>(c, a, tent, state);
-        tent_sat(c, a, (Real*)nullptr);
+        tent_sat<Real, DIM, P, MODE>(c, a, (Real*)nullptr);
         bool bad = false;
         for (int idx = threadIdx.x; idx < c.ns * NF * NB; idx += NT) {
             const int k = idx / (NF * NB), rr = idx - k * NF * NB, s = rr / NB, b = rr - s * NB;
@@ -774,7 +792,7 @@ __device__ bool tent_dag_step(unsigned char* smem, const KArgs& a, const PArgs& 
     return true;
 }
 
-template <typename Real, int DIM, int P>
+template <typename Real, int DIM, int P, int MODE = 0>
 __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::value)
     tent_persistent_kernel(const KArgs a, const PArgs pa) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -788,7 +806,7 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::va
         __syncthreads();
         const long long tent = s_ticket;
         if (tent >= pa.n_tents) break;
-        if (!tent_dag_step<Real, DIM, P>(smem, a, pa, tent, &s_abort)) break;
+        if (!tent_dag_step<Real, DIM, P, MODE>(smem, a, pa, tent, &s_abort)) break;
     }
 }
 
@@ -831,6 +849,236 @@ __global__ void __launch_bounds__(Shape<DIM, 4>::NT, sizeof(Real) == 4 ? 2 : 1) 
             default: ok = tent_dag_step<Real, DIM, 4>(smem, a, pa, tent, &s_abort); break;
         }
         if (!ok) break;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Tensor-core contractions (warp-level m16n8k8 TF32 MMA, FP32 accumulate), 3D.  One warp
+// owns a pair of elements with the same local index j (both share the A operands):
+// N = 2 tiles of 8 columns (the 6 fields of each element), M over basis functions / facet
+// modes, K over basis functions / facet modes.  Operands: A from the fragment-ordered tables
+// (one 16-byte load per lane), B from the shared-memory state (converted to TF32).  The curl
+// combination and the mass solve need all 6 fields of one coefficient, spread over the 3
+// lanes of a quad: they are gathered with quad shuffles.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void mma_tf32(float d[4], const uint32_t a[4], const uint32_t b[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// B fragment (k8 x n8) from a row-major [n][k] source: rows n = g (< nrow), k = k0 + t, k0 + t + 4 (< kmax)
+template <int MODE>
+__device__ __forceinline__ void load_b(const float* row, bool valid, int k, int kmax, uint32_t hi[2], uint32_t lo[2]) {
+    const float x0 = (valid && k < kmax) ? row[k] : 0.f;
+    const float x1 = (valid && k + 4 < kmax) ? row[k + 4] : 0.f;
+    hi[0] = to_tf32(x0);
+    hi[1] = to_tf32(x1);
+    if constexpr (MODE == 2) {
+        lo[0] = to_tf32(x0 - __uint_as_float(hi[0]));
+        lo[1] = to_tf32(x1 - __uint_as_float(hi[1]));
+    }
+}
+template <int MODE>
+__device__ __forceinline__ void mma_mode(float d[4], const float4& ah, const float4& al, const uint32_t bh[2],
+                                         const uint32_t bl[2]) {
+    const uint32_t a[4] = {__float_as_uint(ah.x), __float_as_uint(ah.y), __float_as_uint(ah.z), __float_as_uint(ah.w)};
+    mma_tf32(d, a, bh);
+    if constexpr (MODE == 2) {
+        const uint32_t l[4] = {__float_as_uint(al.x), __float_as_uint(al.y), __float_as_uint(al.z),
+                               __float_as_uint(al.w)};
+        mma_tf32(d, a, bl);
+        mma_tf32(d, l, bh);
+    }
+}
+
+template <int P>
+struct TcShape {
+    static constexpr int NB = (P + 1) * (P + 2) * (P + 3) / 6;
+    static constexpr int NFB = (P + 1) * (P + 2) / 2;
+    static constexpr int MT = (NB + 15) / 16;      // m16 tiles over basis functions
+    static constexpr int KT = (NB + 7) / 8;        // k8 steps over basis functions
+    static constexpr int KTL = (NFB + 7) / 8;      // k8 steps over facet modes
+};
+
+template <typename Real, int DIM, int P, int MODE>
+__device__ void tent_traces_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real* Ucur, Real* tr) {
+    static_assert(DIM == 3 && sizeof(Real) == 4, "tensor-core path: 3D FP32 state");
+    using Sh = Shape<DIM, P>;
+    using Tc = TcShape<P>;
+    constexpr int NF = Sh::NF, NB = Sh::NB, NFB = Sh::NFB, NBP = Sh::NBP, NFBP = Sh::NFBP;
+    constexpr int ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int npair = *c.sNpair;
+    for (int item = warp; item < npair * DIM; item += nwarps) {
+        const int pi = item / DIM, fi = item - pi * DIM;
+        const int k0 = c.sPair[2 * pi], kk1 = c.sPair[2 * pi + 1];
+        const int ke[2] = {k0, kk1 >= 0 ? kk1 : k0};
+        const int j = c.sJ[k0];
+        const int f = fi + (fi >= j ? 1 : 0);
+        float acc[2][4] = {};
+#pragma unroll
+        for (int kt = 0; kt < Tc::KT; ++kt) {
+            const float4 ah = __ldg(a.Trf + ((size_t)f * Tc::KT + kt) * 32 + lane);
+            float4 al = ah;
+            if constexpr (MODE == 2) al = __ldg(a.Trf_lo + ((size_t)f * Tc::KT + kt) * 32 + lane);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                uint32_t bh[2], bl[2];
+                load_b<MODE>(Ucur + ke[nt] * ESZ + g * NBP, g < NF, 8 * kt + t, NB, bh, bl);
+                mma_mode<MODE>(acc[nt], ah, al, bh, bl);
+            }
+        }
+        // acc[nt]: rows c = g (cols s = 2t, 2t+1), c = g + 8
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            if (nt == 1 && kk1 < 0) break;
+            const int k = ke[nt];
+            const Real sc = c.sTrs[k];
+            Real* out = tr + k * TSZ + fi * NF * NFBP;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int cc = g + 8 * h;
+                if (cc < NFB && t < 3) {
+                    out[(2 * t) * NFBP + cc] = acc[nt][2 * h] * sc;
+                    out[(2 * t + 1) * NFBP + cc] = acc[nt][2 * h + 1] * sc;
+                }
+            }
+        }
+    }
+}
+
+template <typename Real, int DIM, int P, int MODE>
+__device__ void tent_stage_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, const Real* Ucur, Real* Unext,
+                              const Real* tr) {
+    static_assert(DIM == 3 && sizeof(Real) == 4, "tensor-core path: 3D FP32 state");
+    using Sh = Shape<DIM, P>;
+    using Tc = TcShape<P>;
+    constexpr int NF = Sh::NF, NB = Sh::NB, NFB = Sh::NFB, NBP = Sh::NBP, NFBP = Sh::NFBP, NV = Sh::NV;
+    constexpr int ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const unsigned full = 0xffffffffu;
+    const float cn = (float)a.taylor[n];
+    const float nn = (float)n;
+    const int npair = *c.sNpair;
+    for (int item = warp; item < npair * Tc::MT; item += nwarps) {
+        const int pi = item / Tc::MT, mt = item - pi * Tc::MT;
+        const int k0 = c.sPair[2 * pi], kk1 = c.sPair[2 * pi + 1];
+        const int ke[2] = {k0, kk1 >= 0 ? kk1 : k0};
+        const int j = c.sJ[k0];
+        // volume: P_l[a][(s, e)] = sum_b S_{j,l}[a][b] U_e[s][b]
+        float Pv[3][2][4] = {};
+#pragma unroll
+        for (int kt = 0; kt < Tc::KT; ++kt) {
+            uint32_t bh[2][2], bl[2][2];
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+                load_b<MODE>(Ucur + ke[nt] * ESZ + g * NBP, g < NF, 8 * kt + t, NB, bh[nt], bl[nt]);
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+                const size_t fr = (((size_t)j * 3 + l) * Tc::MT + mt) * Tc::KT + kt;
+                const float4 ah = __ldg(a.Sf + fr * 32 + lane);
+                float4 al = ah;
+                if constexpr (MODE == 2) al = __ldg(a.Sf_lo + fr * 32 + lane);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) mma_mode<MODE>(Pv[l][nt], ah, al, bh[nt], bl[nt]);
+            }
+        }
+        // lift: Lc[a][(r, e)] = sum_{fi, c} L_{j,f}[a][c] F_e[fi][r][c]
+        float Lc[2][4] = {};
+#pragma unroll
+        for (int fi = 0; fi < DIM; ++fi) {
+            const int f = fi + (fi >= j ? 1 : 0);
+#pragma unroll
+            for (int kt = 0; kt < Tc::KTL; ++kt) {
+                const size_t fr = (((size_t)j * NV + f) * Tc::MT + mt) * Tc::KTL + kt;
+                const float4 ah = __ldg(a.Lfr + fr * 32 + lane);
+                float4 al = ah;
+                if constexpr (MODE == 2) al = __ldg(a.Lfr_lo + fr * 32 + lane);
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    uint32_t bh[2], bl[2];
+                    load_b<MODE>(tr + ke[nt] * TSZ + fi * NF * NFBP + g * NFBP, g < NF, 8 * kt + t, NFB, bh, bl);
+                    mma_mode<MODE>(Lc[nt], ah, al, bh, bl);
+                }
+            }
+        }
+        // per element and row half: curl combination, Taylor accumulation, mass solve
+        const int src0 = lane & ~3;
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+            const int k = ke[nt];
+            const float* ac = c.sAc + k * DIM * 3;
+            const float* U = Ucur + k * ESZ;
+            const float* gd = c.sGd + 3 * k;
+            const float* Gi = c.sGi + k * NF * NF;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int av = 16 * mt + g + 8 * h;
+                float Pf[3][6];
+#pragma unroll
+                for (int l = 0; l < 3; ++l)
+#pragma unroll
+                    for (int u = 0; u < 3; ++u) {
+                        Pf[l][2 * u] = __shfl_sync(full, Pv[l][nt][2 * h], src0 + u);
+                        Pf[l][2 * u + 1] = __shfl_sync(full, Pv[l][nt][2 * h + 1], src0 + u);
+                    }
+                float Yf[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+                for (int l = 0; l < 3; ++l) {
+                    const float ax = ac[3 * l], ay = ac[3 * l + 1], az = ac[3 * l + 2];
+                    const float* Pl = Pf[l];
+                    Yf[0] -= ay * Pl[5] - az * Pl[4];   // -a x P_H
+                    Yf[1] -= az * Pl[3] - ax * Pl[5];
+                    Yf[2] -= ax * Pl[4] - ay * Pl[3];
+                    Yf[3] += ay * Pl[2] - az * Pl[1];   //  a x P_E
+                    Yf[4] += az * Pl[0] - ax * Pl[2];
+                    Yf[5] += ax * Pl[1] - ay * Pl[0];
+                }
+                // subtract the lift: this lane holds columns r = 2t, 2t+1
+                float y0 = (t < 3 ? Yf[2 * t] : 0.f) - Lc[nt][2 * h];
+                float y1 = (t < 3 ? Yf[2 * t + 1] : 0.f) - Lc[nt][2 * h + 1];
+                float Yn[6];
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    Yn[2 * u] = __shfl_sync(full, y0, src0 + u);
+                    Yn[2 * u + 1] = __shfl_sync(full, y1, src0 + u);
+                }
+                const bool own = (nt == 0 || kk1 >= 0) && av < NB && t < 3;
+                if (own) {
+                    float* Y = c.sY + k * ESZ + av;
+                    Y[(2 * t) * NBP] += cn * y0;
+                    Y[(2 * t + 1) * NBP] += cn * y1;
+                    if (n < a.q) {
+                        const float E0 = U[0 * NBP + av], E1 = U[1 * NBP + av], E2 = U[2 * NBP + av];
+                        const float H0 = U[3 * NBP + av], H1 = U[4 * NBP + av], H2 = U[5 * NBP + av];
+                        float r6[6];
+                        r6[0] = Yn[0] + nn * (H1 * gd[2] - H2 * gd[1]);
+                        r6[1] = Yn[1] + nn * (H2 * gd[0] - H0 * gd[2]);
+                        r6[2] = Yn[2] + nn * (H0 * gd[1] - H1 * gd[0]);
+                        r6[3] = Yn[3] - nn * (E1 * gd[2] - E2 * gd[1]);
+                        r6[4] = Yn[4] - nn * (E2 * gd[0] - E0 * gd[2]);
+                        r6[5] = Yn[5] - nn * (E0 * gd[1] - E1 * gd[0]);
+#pragma unroll
+                        for (int q = 0; q < 2; ++q) {
+                            const int r = 2 * t + q;
+                            float acc = 0;
+#pragma unroll
+                            for (int s = 0; s < 6; ++s) acc += Gi[r * NF + s] * r6[s];
+                            Unext[k * ESZ + r * NBP + av] = acc;
+                        }
+                    }
+                }
+            }
+        }
     }
 }
 

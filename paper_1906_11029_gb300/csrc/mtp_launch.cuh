@@ -11,36 +11,36 @@ using PrepareFn = cudaError_t (*)(int max_patch, size_t* smem_bytes);
 using PersistentFn = cudaError_t (*)(const KArgs&, const PArgs&, int grid, cudaStream_t st);
 using PersistentPrepFn = cudaError_t (*)(int max_patch, int* blocks_per_sm);
 
-template <typename Real, int DIM, int P>
+template <typename Real, int DIM, int P, int MODE = 0>
 cudaError_t prepare_tent_kernel(int max_patch, size_t* smem_bytes) {
     SmemLayout<Real, DIM, P> lay(max_patch);
     *smem_bytes = lay.bytes;
-    return cudaFuncSetAttribute(tent_layer_kernel<Real, DIM, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(tent_layer_kernel<Real, DIM, P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)lay.bytes);
 }
 
-template <typename Real, int DIM, int P>
+template <typename Real, int DIM, int P, int MODE = 0>
 cudaError_t launch_tent_kernel(const KArgs& a, int64_t t0, int n_tents, int n_rhs, cudaStream_t st) {
     SmemLayout<Real, DIM, P> lay(a.max_patch);
     dim3 grid(n_tents, n_rhs);
-    tent_layer_kernel<Real, DIM, P><<<grid, Shape<DIM, P>::NT, lay.bytes, st>>>(a, t0);
+    tent_layer_kernel<Real, DIM, P, MODE><<<grid, Shape<DIM, P>::NT, lay.bytes, st>>>(a, t0);
     return cudaGetLastError();
 }
 
-template <typename Real, int DIM, int P>
+template <typename Real, int DIM, int P, int MODE = 0>
 cudaError_t prepare_persistent_kernel(int max_patch, int* blocks_per_sm) {
     SmemLayout<Real, DIM, P> lay(max_patch);
-    cudaError_t e = cudaFuncSetAttribute(tent_persistent_kernel<Real, DIM, P>,
+    cudaError_t e = cudaFuncSetAttribute(tent_persistent_kernel<Real, DIM, P, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.bytes);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tent_persistent_kernel<Real, DIM, P>,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, tent_persistent_kernel<Real, DIM, P, MODE>,
                                                          Shape<DIM, P>::NT, lay.bytes);
 }
 
-template <typename Real, int DIM, int P>
+template <typename Real, int DIM, int P, int MODE = 0>
 cudaError_t launch_persistent_kernel(const KArgs& a, const PArgs& pa, int grid, cudaStream_t st) {
     SmemLayout<Real, DIM, P> lay(a.max_patch);
-    tent_persistent_kernel<Real, DIM, P><<<grid, Shape<DIM, P>::NT, lay.bytes, st>>>(a, pa);
+    tent_persistent_kernel<Real, DIM, P, MODE><<<grid, Shape<DIM, P>::NT, lay.bytes, st>>>(a, pa);
     return cudaGetLastError();
 }
 
@@ -54,6 +54,8 @@ struct KernelEntry {
 // entries[dim - 2][p - 1]
 void kernel_table_f64(KernelEntry entries[2][4]);
 void kernel_table_f32(KernelEntry entries[2][4]);
+// tensor-core modes (3D only): entries[mode - 1][p - 1]
+void kernel_table_tc(KernelEntry entries[2][4]);
 
 struct AdjArgs;
 using AdjLaunchFn = cudaError_t (*)(const AdjArgs&, int64_t t0, int n_tents, int n_rhs, cudaStream_t st);

@@ -205,3 +205,28 @@ def test_fp32_error_against_discretisation_error_cube16():
     assert e_disc < 1e-4
     assert e_prec <= 1e-5
     assert e_prec <= 0.35 * e_disc
+
+
+# Tensor-core modes (3D): TF32 operands have a unit roundoff of 2^-11 ~ 4.9e-4, so a tent
+# (m q = 12..40 stages of contractions over up to 3 x 35 products) stays within ~1e-3 relative;
+# the 3-term hi + lo split recovers FP32-level products (tolerance as FP32).
+TC_TOL = {mtp.MTP_TF32: 3e-3, mtp.MTP_TF32X3: 1e-5}
+
+
+@pytest.mark.parametrize("precision", [mtp.MTP_TF32, mtp.MTP_TF32X3])
+@pytest.mark.parametrize("name", ["cube_n2_p1", "cube_n2_p2", "cube_n2_p3", "cube_n2_p4", "graded_n3_p2"])
+def test_tensor_core_modes_match_oracle(name, precision):
+    w = _CASES[name]()
+    vals0, ref, _, _ = _oracle(name)
+    out, e0, e1 = _gpu_full(w, precision, vals0)
+    err = rel_l2(out[0], ref)
+    print(f"{name} mode {precision}: rel l2 {err:.2e}")
+    assert err <= TC_TOL[precision], (name, precision, err)
+
+
+@pytest.mark.parametrize("precision", [mtp.MTP_TF32, mtp.MTP_TF32X3])
+def test_tensor_core_modes_graded32_single_layer(precision):
+    w = S.graded_sphere(32, 4, 0.5)
+    err = _single_layer_check(w, precision, 0.3, 3, 202)
+    print(f"graded32 single layer mode {precision}: {err:.2e}")
+    assert err <= TC_TOL[precision], err
