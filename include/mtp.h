@@ -52,6 +52,9 @@ extern "C" {
 /* mtp_options.flags bits */
 #define MTP_FLAG_LAYER_LAUNCHES 1   /* mtp_evolve: one launch per layer (CUDA graph) instead of the
                                        persistent DAG-walking kernel */
+#define MTP_FLAG_TEST_STALL     2   /* failure injection for tests: the persistent evolve never
+                                       publishes the completion of its first tent and waits at most
+                                       0.2 s, so it must return MTP_ETIMEOUT */
 
 /* precision of the state and of the operator arithmetic */
 #define MTP_FP64   0   /* FP64 state and arithmetic */

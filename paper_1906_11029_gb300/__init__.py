@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libmtp.so")
 MTP_OK, MTP_EINVAL, MTP_EMESH, MTP_ECAUSAL = 0, -1, -2, -3
 MTP_ENOMEM, MTP_ECUDA, MTP_ETIMEOUT, MTP_ENUMERIC, MTP_EUNSUPPORTED = -4, -5, -6, -7, -8
 MTP_FP64, MTP_FP32, MTP_TF32, MTP_TF32X3 = 0, 1, 2, 3
-MTP_FLAG_LAYER_LAUNCHES = 1
+MTP_FLAG_LAYER_LAUNCHES, MTP_FLAG_TEST_STALL = 1, 2
 _CODES = {0: "MTP_OK", -1: "MTP_EINVAL", -2: "MTP_EMESH", -3: "MTP_ECAUSAL", -4: "MTP_ENOMEM",
           -5: "MTP_ECUDA", -6: "MTP_ETIMEOUT", -7: "MTP_ENUMERIC", -8: "MTP_EUNSUPPORTED"}
 

@@ -493,8 +493,9 @@ int device_evolve(Tents& t, void* state, int64_t lb, int64_t le, bool use_graph,
         pa.adj_ptr = d.adj_ptr;
         pa.adj = d.adj;
         pa.tent_layer = d.tent_layer;
-        pa.timeout_ns = 10000000000LL;     // 10 s per wait
+        pa.timeout_ns = (m.flags & MTP_FLAG_TEST_STALL) ? 200000000LL : 10000000000LL;   // 0.2 s / 10 s per wait
         pa.n_rhs = m.n_rhs;
+        pa.withhold_first = (m.flags & MTP_FLAG_TEST_STALL) ? 1 : 0;
         CUDA_TRY(ke.persistent(a, pa, grid, st));
     } else if (use_graph && full) {
         if (!d.exec || d.graph_state != state) {
@@ -701,6 +702,7 @@ int device_batch_evolve(Batch& b, void* const* states, void* stream) {
         pa[i].tent_layer = dt.tent_layer;
         pa[i].timeout_ns = 10000000000LL;
         pa[i].n_rhs = m.n_rhs;
+        pa[i].withhold_first = 0;
         CUDA_TRY(cudaMemsetAsync(dt.tau, 0, sizeof(double) * m.nv, st));   // flat front t = 0
         CUDA_TRY(cudaMemsetAsync(dt.cnt, 0, sizeof(int) * m.nv, st));
     }

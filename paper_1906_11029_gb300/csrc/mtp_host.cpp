@@ -458,7 +458,7 @@ int mtp_mesh_create(int dim, int64_t n_verts, const double* vertices, int64_t n_
     if (opts->precision >= MTP_TF32 && dim != 3)
         return set_error(MTP_EUNSUPPORTED, "tensor-core precisions are built for 3D meshes");
     if (opts->n_rhs < 0 || opts->n_rhs > 4096) return set_error(MTP_EINVAL, "n_rhs must be in 0..4096");
-    if (opts->flags & ~MTP_FLAG_LAYER_LAUNCHES) return set_error(MTP_EINVAL, "unknown flag bits");
+    if (opts->flags & ~(MTP_FLAG_LAYER_LAUNCHES | MTP_FLAG_TEST_STALL)) return set_error(MTP_EINVAL, "unknown flag bits");
     auto h = std::make_unique<mtp_mesh>();
     int rc = build_mesh(dim, n_verts, vertices, n_elems, elements, eps, mu, *opts, h->m);
     if (rc != MTP_OK) return rc;

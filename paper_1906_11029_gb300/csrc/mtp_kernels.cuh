@@ -323,7 +323,12 @@ __device__ void tent_ginv(TentCtx<Real, DIM, P>& c, const KArgs& a, int i) {
         double g[3];
         for (int q = 0; q < 3; ++q) g[q] = c.sGphi[3 * k + q] + ti * c.sGdel[3 * k + q];
         const double eps = c.sMat[2 * k], mu = c.sMat[2 * k + 1];
-        if (!(g[0] * g[0] + g[1] * g[1] + g[2] * g[2] < eps * mu)) atomicExch(a.err, 1);
+        if (!(g[0] * g[0] + g[1] * g[1] + g[2] * g[2] < eps * mu)) atomicCAS(a.err, 0, 1);
+        if (i == 0) {   // grad phi is affine in t, so bottom and top bound the whole tent
+            double gt[3];
+            for (int q = 0; q < 3; ++q) gt[q] = c.sGphi[3 * k + q] + c.sGdel[3 * k + q];
+            if (!(gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2] < eps * mu)) atomicCAS(a.err, 0, 1);
+        }
         for (int s = 0; s < NF; ++s) {
             double w[6] = {0, 0, 0, 0, 0, 0}, o[6];
             w[field6<DIM>(s)] = 1.0;
@@ -698,7 +703,7 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::va
         if (!isfinite((double)v)) bad = true;
         state[(int64_t)a.patch_elem[c.pb + k] * NF * NB + r] = v;
     }
-    if (bad) atomicExch(a.err, 2);
+    if (bad) atomicCAS(a.err, 0, 2);
     if (threadIdx.x == 0 && blockIdx.y == 0) a.tau[c.V] = a.tent_tt[tent];
 }
 
@@ -720,6 +725,7 @@ struct PArgs {
     const int32_t* tent_layer;
     long long timeout_ns;
     int n_rhs;
+    int withhold_first;            // failure injection: never publish ticket 0's completion
 };
 
 __device__ __forceinline__ int load_acquire(const int* p) {
@@ -779,11 +785,11 @@ __device__ bool tent_dag_step(unsigned char* smem, const KArgs& a, const PArgs& 
             if (!isfinite((double)v)) bad = true;
             state[(int64_t)a.patch_elem[c.pb + k] * NF * NB + rr] = v;
         }
-        if (bad) atomicExch(a.err, 2);
+        if (bad) atomicCAS(a.err, 0, 2);
         __threadfence();                       // publish this thread's state writes (gpu scope)
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !(pa.withhold_first && tent == 0)) {
         a.tau[V] = a.tent_tt[tent];
         __threadfence();
         atomicAdd(pa.cnt + V, 1);

@@ -85,3 +85,21 @@ def test_pitcher_bit_exact_with_wavespeed():
 @pytest.mark.slow
 def test_pitcher_bit_exact_cube16():
     _compare(S.cube_mode(16, 3, 1.0))
+
+
+def test_patch_larger_than_build_limit_is_rejected():
+    # a 2D fan of 20 triangles around one vertex: patch 20 > the 2D limit (16)
+    k = 20
+    ang = np.linspace(0, 2 * np.pi, k, endpoint=False)
+    v = np.vstack([[0.0, 0.0], np.stack([np.cos(ang), np.sin(ang)], 1)])
+    e = np.array([[0, 1 + i, 1 + (i + 1) % k] for i in range(k)], np.int32)
+    with pytest.raises(mtp.MtpError) as ex:
+        mtp.Mesh(2, v, e, np.ones(k), np.ones(k), p=2)
+    assert ex.value.code == mtp.MTP_EUNSUPPORTED
+
+
+def test_tensor_core_precision_is_3d_only():
+    v, e = S.square_mesh(2)
+    with pytest.raises(mtp.MtpError) as ex:
+        mtp.Mesh(2, v, e, np.ones(len(e)), np.ones(len(e)), p=2, precision=mtp.MTP_TF32)
+    assert ex.value.code == mtp.MTP_EUNSUPPORTED
