@@ -264,6 +264,55 @@ def run_many(args):
                                  "setup_s": setup_s}}))
 
 
+def lattice_interpolation(dim, p_from, p_to):
+    """Matrix taking values of a degree-p_from polynomial at its lattice points to its values at
+    the degree-p_to lattice points of the same simplex (exact; monomials in the reference
+    coordinates of the sorted-vertex lattice)."""
+    import itertools
+    import mtp_synth as S
+    exps = [e for e in itertools.product(range(p_from + 1), repeat=dim) if sum(e) <= p_from]
+
+    def vander(p):
+        pts = S.lattice_multi_indices(dim, p).astype(float) / p
+        return np.array([[np.prod(pt ** np.array(e)) for e in exps] for pt in pts])
+    return vander(p_to) @ np.linalg.inv(vander(p_from))
+
+
+def run_equal_error(args):
+    """Discretisation error of the p = 4 graded workload estimated against p = 5 on the same mesh
+    and tents (u4 interpolated exactly to the p = 5 lattice), next to the distance of each
+    FP32-state mode from the FP32 SIMT path and from each other."""
+    import torch
+    import mtp_synth as S
+    import paper_1906_11029_gb300 as mtp
+    w4 = make_workload(args.workload)
+    out, times = {}, {}
+    for p, prec in ((5, mtp.MTP_FP32), (4, mtp.MTP_FP32), (4, mtp.MTP_TF32), (4, mtp.MTP_TF32X3)):
+        w = S.graded_sphere(32, p, 0.5) if args.workload == "graded" else w4
+        mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=p, precision=prec)
+        tents = mesh.pitch(w.T, w.causality)
+        st = mesh.state_from_lattice(torch.tensor(initial_lattice(w)[None], device="cuda"))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        tents.evolve(st)
+        b.record()
+        torch.cuda.synchronize()
+        times[(p, prec)] = a.elapsed_time(b)
+        out[(p, prec)] = mesh.state_to_lattice(st).cpu().numpy()[0]
+        del mesh, tents, st
+    I = lattice_interpolation(3, 4, 5)
+    u5 = out[(5, mtp.MTP_FP32)]
+    up = lambda u4: np.einsum("kl,elf->ekf", I, u4)
+    ref = out[(4, mtp.MTP_FP32)]
+    rel = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))
+    names = {mtp.MTP_FP32: "fp32", mtp.MTP_TF32: "tf32", mtp.MTP_TF32X3: "tf32x3"}
+    res = {"workload": w4.name, "e_disc_p4_vs_p5": rel(up(ref), u5),
+           "ms": {f"p{p}_{names[q]}": v for (p, q), v in times.items()}}
+    for q in (mtp.MTP_TF32, mtp.MTP_TF32X3):
+        res[f"{names[q]}_vs_fp32"] = rel(out[(4, q)], ref)
+    print(json.dumps(res))
+
+
 def run_mtp(args):
     import torch
     import paper_1906_11029_gb300 as mtp
@@ -443,6 +492,7 @@ def main():
     ap.add_argument("--cpu-worker", default=None)
     ap.add_argument("--profile-window", default=None, help="a:b -> apply layers [a, b) once and exit")
     ap.add_argument("--profile-evolve", action="store_true", help="run one full evolve and exit")
+    ap.add_argument("--equal-error", action="store_true", help="p=4 precision modes against p=5")
     ap.add_argument("--seed", type=int, default=7)
     args = ap.parse_args()
     if args.cpu_worker:
@@ -455,6 +505,8 @@ def main():
         return run_profile_evolve(args)
     if args.workload == "many":
         return run_many(args)
+    if args.equal_error:
+        return run_equal_error(args)
     return run_mtp(args)
 
 

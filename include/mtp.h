@@ -47,7 +47,7 @@ extern "C" {
 #define MTP_ECUDA        -5   /* a CUDA runtime call failed (message has the CUDA error) */
 #define MTP_ETIMEOUT     -6   /* a bounded device-side wait expired */
 #define MTP_ENUMERIC     -7   /* NaN / Inf detected */
-#define MTP_EUNSUPPORTED -8   /* combination not built (e.g. degree > 4, patch too large) */
+#define MTP_EUNSUPPORTED -8   /* combination not built (e.g. degree > 5, patch too large) */
 
 /* mtp_options.flags bits */
 #define MTP_FLAG_LAYER_LAUNCHES 1   /* mtp_evolve: one launch per layer (CUDA graph) instead of the
@@ -69,7 +69,7 @@ typedef struct mtp_tents* mtp_tents_t;
 typedef struct mtp_batch* mtp_batch_t;
 
 typedef struct {
-    int p;          /* polynomial degree of V_h, 1..4 (Sec. 3, DG space)                   */
+    int p;          /* polynomial degree of V_h, 1..5 (Sec. 3, DG space)                   */
     int q;          /* SAT stages; 0 selects p+1 (Sec. 5.1)                                */
     int m;          /* SAT sub-intervals per tent; 0 selects 2p (Sec. 5.1)                 */
     int precision;  /* MTP_FP64, MTP_FP32, MTP_TF32 or MTP_TF32X3                            */
@@ -155,7 +155,7 @@ int mtp_evolve_host(mtp_tents_t tents, const void* state_in_host, void* state_ou
 
 /* Many independent problems evolved in one persistent launch (Sec. 2: tents of different
  * meshes are trivially independent).  tents[n]: pitched tent lists of meshes with the same
- * dimension and precision, any degrees 1..4 (default q = p + 1, m = 2p), any n_rhs each.
+ * dimension and precision, any degrees 1..5 (default q = p + 1, m = 2p), any n_rhs each.
  * Tents of all instances are taken in (layer, instance, vertex) order; each instance keeps its
  * own dependency counters.  The batch refers to the tents handles: destroy it first. */
 int mtp_batch_create(int64_t n, const mtp_tents_t* tents, mtp_batch_t* out);

@@ -8,6 +8,7 @@ template <typename Real, int DIM, int P>
 cudaError_t prepare_adjoint_kernel(int max_patch, size_t* smem_bytes) {
     AdjLayout<Real, DIM, P> lay(max_patch);
     *smem_bytes = lay.bytes;
+    if (!smem_fits(lay.bytes)) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(tent_adjoint_kernel<Real, DIM, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)lay.bytes);
 }
@@ -28,15 +29,15 @@ int64_t adjoint_tape_stride(int max_patch, int m, int q) {
 
 #define ADJ_ENTRY(REAL, D, P) {launch_adjoint_kernel<REAL, D, P>, prepare_adjoint_kernel<REAL, D, P>, adjoint_tape_stride<REAL, D, P>}
 
-void adjoint_table(AdjEntry e[2][2][4]) {
-    AdjEntry t[2][2][4] = {
-        {{ADJ_ENTRY(double, 2, 1), ADJ_ENTRY(double, 2, 2), ADJ_ENTRY(double, 2, 3), ADJ_ENTRY(double, 2, 4)},
-         {ADJ_ENTRY(double, 3, 1), ADJ_ENTRY(double, 3, 2), ADJ_ENTRY(double, 3, 3), ADJ_ENTRY(double, 3, 4)}},
-        {{ADJ_ENTRY(float, 2, 1), ADJ_ENTRY(float, 2, 2), ADJ_ENTRY(float, 2, 3), ADJ_ENTRY(float, 2, 4)},
-         {ADJ_ENTRY(float, 3, 1), ADJ_ENTRY(float, 3, 2), ADJ_ENTRY(float, 3, 3), ADJ_ENTRY(float, 3, 4)}}};
+void adjoint_table(AdjEntry e[2][2][5]) {
+    AdjEntry t[2][2][5] = {
+        {{ADJ_ENTRY(double, 2, 1), ADJ_ENTRY(double, 2, 2), ADJ_ENTRY(double, 2, 3), ADJ_ENTRY(double, 2, 4), ADJ_ENTRY(double, 2, 5)},
+         {ADJ_ENTRY(double, 3, 1), ADJ_ENTRY(double, 3, 2), ADJ_ENTRY(double, 3, 3), ADJ_ENTRY(double, 3, 4), ADJ_ENTRY(double, 3, 5)}},
+        {{ADJ_ENTRY(float, 2, 1), ADJ_ENTRY(float, 2, 2), ADJ_ENTRY(float, 2, 3), ADJ_ENTRY(float, 2, 4), ADJ_ENTRY(float, 2, 5)},
+         {ADJ_ENTRY(float, 3, 1), ADJ_ENTRY(float, 3, 2), ADJ_ENTRY(float, 3, 3), ADJ_ENTRY(float, 3, 4), ADJ_ENTRY(float, 3, 5)}}};
     for (int a = 0; a < 2; ++a)
         for (int b = 0; b < 2; ++b)
-            for (int c = 0; c < 4; ++c) e[a][b][c] = t[a][b][c];
+            for (int c = 0; c < 5; ++c) e[a][b][c] = t[a][b][c];
 }
 
 }  // namespace mtp

@@ -238,7 +238,7 @@ static int device_tents_upload(Tents& t) {
 }
 
 static const KernelEntry& kernel_entry(const Mesh& m) {
-    static KernelEntry f64[2][4], f32[2][4], tc[2][4];
+    static KernelEntry f64[2][5], f32[2][5], tc[2][5];
     static bool init = false;
     if (!init) {
         kernel_table_f64(f64);
@@ -463,7 +463,7 @@ int device_evolve(Tents& t, void* state, int64_t lb, int64_t le, bool use_graph,
     cudaStream_t st = (cudaStream_t)stream;
     const KernelEntry& ke = kernel_entry(m);
     size_t smem = 0;
-    CUDA_TRY(ke.prepare(m.max_patch, &smem));
+    const cudaError_t pe = ke.prepare(m.max_patch, &smem);
     int dev, smem_max;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -471,6 +471,7 @@ int device_evolve(Tents& t, void* state, int64_t lb, int64_t le, bool use_graph,
         return set_error(MTP_EUNSUPPORTED, "tent kernel needs " + std::to_string(smem) +
                                                " bytes of shared memory per block; the device allows " +
                                                std::to_string(smem_max));
+    CUDA_TRY(pe);
     MTP_TRY(set_front(t, lb, d.tau, st));
     CUDA_TRY(cudaMemsetAsync(d.err, 0, sizeof(int), st));
     KArgs a;
@@ -544,21 +545,23 @@ int device_adjoint(Tents& t, const void* state0, const void* lamT, void* lam0, d
     Mesh& m = *t.mesh;
     DeviceTents& d = *t.dev;
     cudaStream_t st = (cudaStream_t)stream;
-    static AdjEntry table[2][2][4];
+    static AdjEntry table[2][2][5];
     static bool init = false;
     if (!init) { adjoint_table(table); init = true; }
     const AdjEntry& ae = table[m.precision == MTP_FP64 ? 0 : 1][m.dim - 2][m.p - 1];
     const KernelEntry& ke = kernel_entry(m);
     size_t smem = 0, smem_f = 0;
-    CUDA_TRY(ae.prepare(m.max_patch, &smem));
-    CUDA_TRY(ke.prepare(m.max_patch, &smem_f));
+    const cudaError_t pa_ = ae.prepare(m.max_patch, &smem);
+    const cudaError_t pf_ = ke.prepare(m.max_patch, &smem_f);
     int dev, smem_max;
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if ((int64_t)smem > smem_max)
+    if ((int64_t)std::max(smem, smem_f) > smem_max)
         return set_error(MTP_EUNSUPPORTED, "adjoint tent kernel needs " + std::to_string(smem) +
                                                " bytes of shared memory per block; the device allows " +
                                                std::to_string(smem_max));
+    CUDA_TRY(pa_);
+    CUDA_TRY(pf_);
     const int64_t nl = (int64_t)t.layer_ptr.size() - 1;
     if (K <= 0) K = std::max<int64_t>(1, (int64_t)std::ceil(std::sqrt((double)nl)));
     K = std::min(K, nl);

@@ -9,7 +9,7 @@
 
 namespace mtp {
 
-constexpr int kMaxDegree = 4;
+constexpr int kMaxDegree = 5;
 constexpr int kMaxPatch3D = 32;   // Kuhn/Freudenthal meshes have 24 tets per interior vertex
 constexpr int kMaxPatch2D = 16;
 

@@ -5,6 +5,7 @@ namespace mtp {
 
 template <typename Real, int DIM>
 cudaError_t prepare_batch_kernel(size_t smem, int* blocks_per_sm) {
+    if (!smem_fits(smem)) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(tent_batch_kernel<Real, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -24,7 +25,8 @@ size_t batch_smem_bytes(int p, int max_patch) {
         case 1: return SmemLayout<Real, DIM, 1>(max_patch).bytes;
         case 2: return SmemLayout<Real, DIM, 2>(max_patch).bytes;
         case 3: return SmemLayout<Real, DIM, 3>(max_patch).bytes;
-        default: return SmemLayout<Real, DIM, 4>(max_patch).bytes;
+        case 4: return SmemLayout<Real, DIM, 4>(max_patch).bytes;
+        default: return SmemLayout<Real, DIM, 5>(max_patch).bytes;
     }
 }
 

@@ -83,7 +83,7 @@ struct Shape {
 // shared-memory footprint up to p = 4; FP64 p >= 3 fits one)
 template <typename Real, int DIM, int P>
 struct MinBlocks {
-    static constexpr int value = (sizeof(Real) == 4 || P <= 2) ? 2 : 1;
+    static constexpr int value = ((sizeof(Real) == 4 && P <= 4) || P <= 2) ? 2 : 1;
 };
 
 template <typename Real>
@@ -816,7 +816,7 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::va
     }
 }
 
-// Many independent problems (meshes of any degree 1..4, same dimension and precision) in one
+// Many independent problems (meshes of any degree 1..5, same dimension and precision) in one
 // persistent launch: tickets run over the merged tent lists ordered by (layer, instance,
 // vertex); each ticket names its instance, whose KArgs / PArgs (own counters) live in global
 // memory.  Instances never wait on each other.
@@ -852,7 +852,8 @@ __global__ void __launch_bounds__(Shape<DIM, 4>::NT, sizeof(Real) == 4 ? 2 : 1) 
             case 1: ok = tent_dag_step<Real, DIM, 1>(smem, a, pa, tent, &s_abort); break;
             case 2: ok = tent_dag_step<Real, DIM, 2>(smem, a, pa, tent, &s_abort); break;
             case 3: ok = tent_dag_step<Real, DIM, 3>(smem, a, pa, tent, &s_abort); break;
-            default: ok = tent_dag_step<Real, DIM, 4>(smem, a, pa, tent, &s_abort); break;
+            case 4: ok = tent_dag_step<Real, DIM, 4>(smem, a, pa, tent, &s_abort); break;
+            default: ok = tent_dag_step<Real, DIM, 5>(smem, a, pa, tent, &s_abort); break;
         }
         if (!ok) break;
     }
@@ -906,6 +907,7 @@ __device__ __forceinline__ void mma_mode(float d[4], const float4& ah, const flo
 
 template <int P>
 struct TcShape {
+    static_assert(P <= 4, "tensor-core traces keep all facet modes in one m16 tile");
     static constexpr int NB = (P + 1) * (P + 2) * (P + 3) / 6;
     static constexpr int NFB = (P + 1) * (P + 2) / 2;
     static constexpr int MT = (NB + 15) / 16;      // m16 tiles over basis functions

@@ -11,10 +11,23 @@ using PrepareFn = cudaError_t (*)(int max_patch, size_t* smem_bytes);
 using PersistentFn = cudaError_t (*)(const KArgs&, const PArgs&, int grid, cudaStream_t st);
 using PersistentPrepFn = cudaError_t (*)(int max_patch, int* blocks_per_sm);
 
+// true when `bytes` of dynamic shared memory fit one block on the current device
+inline bool smem_fits(size_t bytes) {
+    int dev = 0, mx = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&mx, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    return bytes <= (size_t)mx;
+}
+
+// The prepare functions report the block's shared-memory size and, only when it fits the
+// device, raise the kernel's dynamic shared-memory limit (a refused attribute call would leave
+// an error behind for the next launch); the caller turns a size that does not fit into
+// MTP_EUNSUPPORTED.
 template <typename Real, int DIM, int P, int MODE = 0>
 cudaError_t prepare_tent_kernel(int max_patch, size_t* smem_bytes) {
     SmemLayout<Real, DIM, P> lay(max_patch);
     *smem_bytes = lay.bytes;
+    if (!smem_fits(lay.bytes)) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(tent_layer_kernel<Real, DIM, P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)lay.bytes);
 }
@@ -30,6 +43,7 @@ cudaError_t launch_tent_kernel(const KArgs& a, int64_t t0, int n_tents, int n_rh
 template <typename Real, int DIM, int P, int MODE = 0>
 cudaError_t prepare_persistent_kernel(int max_patch, int* blocks_per_sm) {
     SmemLayout<Real, DIM, P> lay(max_patch);
+    if (!smem_fits(lay.bytes)) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(tent_persistent_kernel<Real, DIM, P, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.bytes);
     if (e != cudaSuccess) return e;
@@ -52,10 +66,10 @@ struct KernelEntry {
 };
 
 // entries[dim - 2][p - 1]
-void kernel_table_f64(KernelEntry entries[2][4]);
-void kernel_table_f32(KernelEntry entries[2][4]);
+void kernel_table_f64(KernelEntry entries[2][5]);
+void kernel_table_f32(KernelEntry entries[2][5]);
 // tensor-core modes (3D only): entries[mode - 1][p - 1]
-void kernel_table_tc(KernelEntry entries[2][4]);
+void kernel_table_tc(KernelEntry entries[2][5]);
 
 struct AdjArgs;
 using AdjLaunchFn = cudaError_t (*)(const AdjArgs&, int64_t t0, int n_tents, int n_rhs, cudaStream_t st);
@@ -66,7 +80,7 @@ struct AdjEntry {
     TapeStrideFn tape_stride;
 };
 // entries[precision][dim - 2][p - 1]
-void adjoint_table(AdjEntry entries[2][2][4]);
+void adjoint_table(AdjEntry entries[2][2][5]);
 
 using BatchLaunchFn = cudaError_t (*)(const BatchArgs&, int grid, size_t smem, cudaStream_t st);
 using BatchPrepFn = cudaError_t (*)(size_t smem, int* blocks_per_sm);
@@ -80,7 +94,7 @@ struct BatchEntry {
 void batch_table(BatchEntry entries[2][2]);
 
 #define MTP_KERNEL_TABLE(NAME, REAL)                                                   \
-    void NAME(KernelEntry e[2][4]) {                                                   \
+    void NAME(KernelEntry e[2][5]) {                                                   \
         e[0][0] = {launch_tent_kernel<REAL, 2, 1>, prepare_tent_kernel<REAL, 2, 1>, \
                     launch_persistent_kernel<REAL, 2, 1>, prepare_persistent_kernel<REAL, 2, 1>};   \
         e[0][1] = {launch_tent_kernel<REAL, 2, 2>, prepare_tent_kernel<REAL, 2, 2>, \
@@ -89,6 +103,8 @@ void batch_table(BatchEntry entries[2][2]);
                     launch_persistent_kernel<REAL, 2, 3>, prepare_persistent_kernel<REAL, 2, 3>};   \
         e[0][3] = {launch_tent_kernel<REAL, 2, 4>, prepare_tent_kernel<REAL, 2, 4>, \
                     launch_persistent_kernel<REAL, 2, 4>, prepare_persistent_kernel<REAL, 2, 4>};   \
+        e[0][4] = {launch_tent_kernel<REAL, 2, 5>, prepare_tent_kernel<REAL, 2, 5>, \
+                    launch_persistent_kernel<REAL, 2, 5>, prepare_persistent_kernel<REAL, 2, 5>};   \
         e[1][0] = {launch_tent_kernel<REAL, 3, 1>, prepare_tent_kernel<REAL, 3, 1>, \
                     launch_persistent_kernel<REAL, 3, 1>, prepare_persistent_kernel<REAL, 3, 1>};   \
         e[1][1] = {launch_tent_kernel<REAL, 3, 2>, prepare_tent_kernel<REAL, 3, 2>, \
@@ -97,6 +113,8 @@ void batch_table(BatchEntry entries[2][2]);
                     launch_persistent_kernel<REAL, 3, 3>, prepare_persistent_kernel<REAL, 3, 3>};   \
         e[1][3] = {launch_tent_kernel<REAL, 3, 4>, prepare_tent_kernel<REAL, 3, 4>, \
                     launch_persistent_kernel<REAL, 3, 4>, prepare_persistent_kernel<REAL, 3, 4>};   \
+        e[1][4] = {launch_tent_kernel<REAL, 3, 5>, prepare_tent_kernel<REAL, 3, 5>, \
+                    launch_persistent_kernel<REAL, 3, 5>, prepare_persistent_kernel<REAL, 3, 5>};   \
     }
 
 }  // namespace mtp

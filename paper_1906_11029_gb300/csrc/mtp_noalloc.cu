@@ -94,7 +94,7 @@ extern "C" int mtp_energy_noalloc(const void* state_dev, const double* eps_dev, 
                                   void* stream) {
     if (!state_dev || !eps_dev || !mu_dev || !out_dev) return set_error(MTP_EINVAL, "NULL argument");
     if (dim != 2 && dim != 3) return set_error(MTP_EINVAL, "dim must be 2 or 3");
-    if (p < 1 || p > kMaxDegree) return set_error(MTP_EINVAL, "p must be in 1..4");
+    if (p < 1 || p > kMaxDegree) return set_error(MTP_EINVAL, "p must be in 1..5");
     if (n_elems < 1) return set_error(MTP_EINVAL, "n_elems must be positive");
     if (precision != MTP_FP64 && precision != MTP_FP32) return set_error(MTP_EINVAL, "unknown precision");
     if (n_rhs < 1 || n_rhs > kNoAllocMaxRhs)

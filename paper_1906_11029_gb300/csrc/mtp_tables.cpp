@@ -20,7 +20,7 @@ namespace mtp {
 namespace {
 
 typedef long double ld;
-constexpr int D = 10;  // degrees up to 9 = 2p + 1 for p = 4
+constexpr int D = 12;  // degrees up to 11 = 2p + 1 for p = 5
 
 struct Poly {
     ld c[D][D][D];

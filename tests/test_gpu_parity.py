@@ -46,6 +46,8 @@ _CASES = {
     "cube_n2_p1": lambda: S.cube_mode(2, 1, 0.15),
     "graded_n3_p2": lambda: S.graded_sphere(n=3, p=2, T=0.06, width=0.3),   # eps jump + grading
     "cube_n2_p4": lambda: S.cube_mode(2, 4, 0.04),
+    "te_square_n3_p5": lambda: S.te_square(3, 5, 0.1),
+    "cube_n2_p5": lambda: S.cube_mode(2, 5, 0.015),
 }
 _ORACLE = {}
 
@@ -60,6 +62,13 @@ def _oracle(name):
 @pytest.mark.parametrize("name", list(_CASES))
 def test_full_evolve_matches_oracle(name, precision):
     w = _CASES[name]()
+    if name == "cube_n2_p5" and precision == mtp.MTP_FP64:
+        # a 24-tet patch of degree 5 in FP64 needs more shared memory than one block may have
+        m = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=5, precision=precision)
+        with pytest.raises(mtp.MtpError) as ex:
+            m.pitch(w.T).evolve(m.new_state())
+        assert ex.value.code == mtp.MTP_EUNSUPPORTED
+        return
     vals0, ref, oe0, oe1 = _oracle(name)
     out, e0, e1 = _gpu_full(w, precision, vals0)
     err = rel_l2(out[0], ref)
