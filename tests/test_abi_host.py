@@ -28,7 +28,7 @@ def test_mesh_errors():
     v, e = S.square_mesh(2)
     one = np.ones(len(e))
     with pytest.raises(mtp.MtpError) as ex:
-        mtp.Mesh(2, v, e, one, one, p=5)
+        mtp.Mesh(2, v, e, one, one, p=6)
     assert ex.value.code == mtp.MTP_EUNSUPPORTED
     bad = e.copy()
     bad[0] = [0, 1, 2]                           # collinear vertices (0,0), (.5,0), (1,0)
