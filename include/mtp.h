@@ -141,6 +141,17 @@ int mtp_state_to_lattice(mtp_mesh_t mesh, const void* state_dev, double* vals_de
  * causality, MTP_ENUMERIC on a non-finite result). */
 int mtp_evolve(mtp_tents_t tents, void* state_dev, double T, void* stream);
 
+/* Evolve launch configuration of this tents handle: 0 (default) the persistent DAG walk with as
+ * many CTAs per SM as fit, 1 the DAG walk with one CTA per SM, 2 one launch per layer (CUDA
+ * graph).  MTP_FLAG_LAYER_LAUNCHES on the mesh forces 2. */
+int mtp_tents_set_launch(mtp_tents_t tents, int launch);
+
+/* Autotuner: times the three launch configurations on layers [layer_begin, layer_end) of
+ * scratch_state_dev (overwritten with evolved values) and keeps the fastest for this handle;
+ * *best receives it and ms_out[3] (may be NULL) the measured milliseconds. */
+int mtp_tents_autotune(mtp_tents_t tents, void* scratch_state_dev, int64_t layer_begin,
+                       int64_t layer_end, int* best, double* ms_out, void* stream);
+
 /* Apply only layers [layer_begin, layer_end) to a state that sits on the front just
  * before layer_begin (each vertex at the top of its last earlier tent).  Completion and
  * errors as for mtp_evolve. */

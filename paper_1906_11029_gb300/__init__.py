@@ -29,7 +29,7 @@ _CODES = {0: "MTP_OK", -1: "MTP_EINVAL", -2: "MTP_EMESH", -3: "MTP_ECAUSAL", -4:
 ABI_SYMBOLS = ["mtp_mesh_create", "mtp_mesh_destroy", "mtp_mesh_info", "mtp_pitch_tents",
                "mtp_tents_destroy", "mtp_tents_info", "mtp_tents_get", "mtp_state_from_lattice",
                "mtp_state_to_lattice", "mtp_evolve", "mtp_evolve_layers", "mtp_evolve_host",
-               "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_info", "mtp_batch_evolve",
+               "mtp_tents_set_launch", "mtp_tents_autotune", "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_info", "mtp_batch_evolve",
                "mtp_adjoint", "mtp_energy", "mtp_energy_noalloc", "mtp_probe_rates", "mtp_last_error"]
 
 
@@ -63,6 +63,8 @@ def _load():
         "mtp_evolve": (C.c_int, [P, P, D, P]),
         "mtp_evolve_layers": (C.c_int, [P, P, I64, I64, P]),
         "mtp_evolve_host": (C.c_int, [P, P, P, D, P]),
+        "mtp_tents_set_launch": (C.c_int, [P, C.c_int]),
+        "mtp_tents_autotune": (C.c_int, [P, P, I64, I64, P, P, P]),
         "mtp_batch_create": (C.c_int, [I64, P, C.POINTER(P)]),
         "mtp_batch_destroy": (None, [P]),
         "mtp_batch_info": (C.c_int, [P, P, P, P]),
@@ -182,6 +184,18 @@ def mtp_evolve_layers(tents, state_dev, layer_begin, layer_end, stream=None):
 
 def mtp_evolve_host(tents, state_in, state_out, T, stream=None):
     _check(_lib.mtp_evolve_host(tents, _ptr(state_in), _ptr(state_out), T, _stream(stream)))
+
+
+def mtp_tents_set_launch(h, launch):
+    _check(_lib.mtp_tents_set_launch(h, launch))
+
+
+def mtp_tents_autotune(h, scratch_state, layer_begin, layer_end, stream=None):
+    best = C.c_int()
+    ms = np.zeros(3, np.float64)
+    _check(_lib.mtp_tents_autotune(h, _ptr(scratch_state), layer_begin, layer_end, C.byref(best), _ptr(ms),
+                                   _stream(stream)))
+    return best.value, ms.tolist()
 
 
 def mtp_batch_create(tents_handles):
@@ -315,6 +329,12 @@ class Tents:
 
     def evolve_layers(self, state_dev, layer_begin, layer_end, stream=None):
         mtp_evolve_layers(self.h, state_dev, layer_begin, layer_end, stream)
+
+    def set_launch(self, launch):
+        mtp_tents_set_launch(self.h, launch)
+
+    def autotune(self, scratch_state, layer_begin, layer_end, stream=None):
+        return mtp_tents_autotune(self.h, scratch_state, layer_begin, layer_end, stream)
 
     def evolve_host(self, state_in, state_out, stream=None):
         mtp_evolve_host(self.h, state_in, state_out, self.T, stream)

@@ -477,16 +477,26 @@ int device_evolve(Tents& t, void* state, int64_t lb, int64_t le, bool use_graph,
     KArgs a;
     fill_args(t, state, a);
     const bool full = lb == 0 && le == (int64_t)t.layer_ptr.size() - 1;
-    if (use_graph && full && !(m.flags & MTP_FLAG_LAYER_LAUNCHES)) {
+    const int launch = (m.flags & MTP_FLAG_LAYER_LAUNCHES) ? 2 : t.launch;
+    if (launch != 2 && le > lb) {
         int bpsm = 0, nsm = 0;
         CUDA_TRY(ke.persistent_prepare(m.max_patch, &bpsm));
         CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        const int64_t nt = (int64_t)t.vertex.size();
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)std::max(1, bpsm) * nsm));
-        CUDA_TRY(cudaMemsetAsync(d.cnt, 0, sizeof(int) * m.nv, st));
+        const int64_t t0 = t.layer_ptr[lb], nt = t.layer_ptr[le] - t0;
+        const int cps = launch == 1 ? 1 : std::max(1, bpsm);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)cps * nsm));
+        if (lb == 0) {
+            CUDA_TRY(cudaMemsetAsync(d.cnt, 0, sizeof(int) * m.nv, st));
+        } else {   // tents completed before the window, per vertex
+            std::vector<int> done(m.nv, 0);
+            for (int64_t i = 0; i < t0; ++i) done[t.vertex[i]]++;
+            CUDA_TRY(cudaMemcpyAsync(d.cnt, done.data(), sizeof(int) * m.nv, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(cudaStreamSynchronize(st));
+        }
         CUDA_TRY(cudaMemsetAsync(d.next, 0, sizeof(unsigned long long), st));
         PArgs pa;
         pa.n_tents = nt;
+        pa.ticket0 = t0;
         pa.next = d.next;
         pa.cnt = d.cnt;
         pa.vt_ptr = d.vt_ptr;
@@ -696,6 +706,7 @@ int device_batch_evolve(Batch& b, void* const* states, void* stream) {
         ka[i].err = d.err;
         DeviceTents& dt = *t.dev;
         pa[i].n_tents = (int64_t)t.vertex.size();
+        pa[i].ticket0 = 0;
         pa[i].next = nullptr;
         pa[i].cnt = dt.cnt;
         pa[i].vt_ptr = dt.vt_ptr;
@@ -738,6 +749,38 @@ int device_batch_evolve(Batch& b, void* const* states, void* stream) {
     if (*d.err_host == 2) return set_error(MTP_ENUMERIC, "non-finite value in the evolved state");
     if (*d.err_host == 3) return set_error(MTP_ETIMEOUT, "a tent's wait for its predecessors exceeded the limit");
     if (*d.err_host != 0) return set_error(MTP_ECUDA, "unknown device error word");
+    return MTP_OK;
+}
+
+}  // namespace mtp
+
+namespace mtp {
+
+// Times the three evolve launch configurations on layers [lb, le) of `state` (overwritten) and
+// keeps the fastest in the tents handle.
+int device_autotune(Tents& t, void* state, int64_t lb, int64_t le, int* best, double* ms_out, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    double best_ms = 1e300;
+    int best_c = 0;
+    for (int c = 0; c < 3; ++c) {
+        t.launch = c;
+        MTP_TRY(device_evolve(t, state, lb, le, false, stream));          // warm-up
+        CUDA_TRY(cudaEventRecord(e0, st));
+        MTP_TRY(device_evolve(t, state, lb, le, false, stream));
+        CUDA_TRY(cudaEventRecord(e1, st));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms_out) ms_out[c] = ms;
+        if (ms < best_ms) { best_ms = ms; best_c = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    t.launch = best_c;
+    if (best) *best = best_c;
     return MTP_OK;
 }
 

@@ -579,6 +579,23 @@ int mtp_adjoint(mtp_tents_t tents, const void* state0, const void* lamT, void* l
     MTP_GUARD_END
 }
 
+int mtp_tents_set_launch(mtp_tents_t tents, int launch) {
+    if (!tents) return set_error(MTP_EINVAL, "tents is NULL");
+    if (launch < 0 || launch > 2) return set_error(MTP_EINVAL, "launch must be 0, 1 or 2");
+    tents->t.launch = launch;
+    return MTP_OK;
+}
+
+int mtp_tents_autotune(mtp_tents_t tents, void* scratch_state, int64_t lb, int64_t le, int* best, double* ms_out,
+                       void* stream) {
+    MTP_GUARD_BEGIN
+    if (!tents || !scratch_state) return set_error(MTP_EINVAL, "NULL argument");
+    const int64_t nl = (int64_t)tents->t.layer_ptr.size() - 1;
+    if (lb < 0 || le > nl || lb >= le) return set_error(MTP_EINVAL, "layer window out of bounds or empty");
+    return device_autotune(tents->t, scratch_state, lb, le, best, ms_out, stream);
+    MTP_GUARD_END
+}
+
 int mtp_batch_create(int64_t n, const mtp_tents_t* tents, mtp_batch_t* out) {
     MTP_GUARD_BEGIN
     if (!out) return set_error(MTP_EINVAL, "out is NULL");

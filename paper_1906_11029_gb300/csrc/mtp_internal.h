@@ -72,6 +72,9 @@ struct Tents {
     std::vector<double> t_bot, t_top;
     std::vector<int64_t> layer_ptr;
     double spacetime_dofs = 0;
+    // evolve launch configuration (see mtp_tents_set_launch): 0 DAG walk at the occupancy
+    // limit of CTAs per SM, 1 DAG walk with one CTA per SM, 2 one launch per layer
+    int launch = 0;
     struct DeviceTents* dev = nullptr;
 };
 
@@ -100,6 +103,7 @@ int device_evolve(Tents& t, void* state, int64_t layer_begin, int64_t layer_end,
 int device_evolve_host(Tents& t, const void* in, void* out, void* stream);
 int device_energy(Mesh& m, const void* state, double* out_host, void* stream);
 int device_batch_evolve(Batch& b, void* const* states, void* stream);
+int device_autotune(Tents& t, void* state, int64_t lb, int64_t le, int* best, double* ms_out, void* stream);
 void device_batch_free(Batch& b);
 int device_adjoint(Tents& t, const void* state0, const void* lamT, void* lam0, double* geps, double* gmu,
                    int64_t checkpoint_every, void* stream);

@@ -715,7 +715,8 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::va
 // never depends on CTA residency.  Every wait is bounded (globaltimer deadline); on expiry, or
 // when another CTA has already failed, the CTA sets the error word and stops.
 struct PArgs {
-    int64_t n_tents;
+    int64_t n_tents;               // tickets: tents ticket0 .. ticket0 + n_tents - 1
+    int64_t ticket0;
     unsigned long long* next;      // ticket counter
     int* cnt;                      // completed tents per vertex
     const int64_t* vt_ptr;         // tents of vertex U: layers vt_layer[vt_ptr[U] .. vt_ptr[U+1])
@@ -789,7 +790,7 @@ __device__ bool tent_dag_step(unsigned char* smem, const KArgs& a, const PArgs& 
         __threadfence();                       // publish this thread's state writes (gpu scope)
         __syncthreads();
     }
-    if (threadIdx.x == 0 && !(pa.withhold_first && tent == 0)) {
+    if (threadIdx.x == 0 && !(pa.withhold_first && tent == pa.ticket0)) {
         a.tau[V] = a.tent_tt[tent];
         __threadfence();
         atomicAdd(pa.cnt + V, 1);
@@ -810,9 +811,9 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::va
             s_abort = 0;
         }
         __syncthreads();
-        const long long tent = s_ticket;
-        if (tent >= pa.n_tents) break;
-        if (!tent_dag_step<Real, DIM, P, MODE>(smem, a, pa, tent, &s_abort)) break;
+        const long long ticket = s_ticket;
+        if (ticket >= pa.n_tents) break;
+        if (!tent_dag_step<Real, DIM, P, MODE>(smem, a, pa, pa.ticket0 + ticket, &s_abort)) break;
     }
 }
 

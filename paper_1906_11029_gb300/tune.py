@@ -1,0 +1,87 @@
+"""Autotuner: per GPU, dimension and degree, pick the fastest kernel configuration on a short
+window of layers and cache the choice.
+
+Two levels:
+
+* launch configuration of a tents handle (`mtp_tents_autotune`, native): persistent DAG walk
+  with the occupancy limit of CTAs per SM, DAG walk with one CTA per SM, or one launch per layer;
+* contraction variant within an accuracy class (here): for FP32-level accuracy the SIMT FP32
+  kernels or the tensor-core 3xTF32 split; for "tf32" accuracy additionally plain TF32 tensor
+  cores.  Variants are timed on the same layer window of the caller's workload.
+
+Choices are cached in a JSON file (default ``~/.cache/paper_1906_11029_gb300/tune.json``)
+keyed by GPU name, dimension, degree, accuracy class and largest patch size.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+
+from . import MTP_FP32, MTP_TF32, MTP_TF32X3, Mesh
+
+CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1906_11029_gb300", "tune.json")
+LAUNCH_NAMES = ["dag_walk", "dag_walk_1cta", "layer_launches"]
+
+
+def _key(dim, p, accuracy, max_patch):
+    import torch
+    name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+    return f"{name}|dim{dim}|p{p}|{accuracy}|mp{max_patch}"
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _save(path, data):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    tmp = path + ".tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def candidates(dim, p, accuracy):
+    """Precision variants that meet the accuracy class on this build."""
+    if accuracy == "fp32":
+        return [MTP_FP32] + ([MTP_TF32X3] if dim == 3 and p <= 4 else [])
+    if accuracy == "tf32":
+        return [MTP_FP32] + ([MTP_TF32X3, MTP_TF32] if dim == 3 and p <= 4 else [])
+    raise ValueError("accuracy must be 'fp32' or 'tf32'")
+
+
+def autotune(dim, vertices, elements, eps, mu, p, T, lattice_values, accuracy="fp32",
+             causality_factor=0.5, window=(0.1, 0.02), cache=CACHE, force=False):
+    """Return (precision, launch, record) for this workload.  ``lattice_values``: initial
+    lattice values (as for Mesh.state_from_lattice) used as the scratch state; ``window``:
+    (start, length) of the timed layer window as fractions of the layer count."""
+    import torch
+    data = _load(cache)
+    probe = Mesh(dim, vertices, elements, eps, mu, p=p, precision=MTP_FP32)
+    key = _key(dim, p, accuracy, probe.info["max_patch"])
+    if key in data and not force:
+        rec = data[key]
+        return rec["precision"], rec["launch"], rec
+    results = []
+    vals = torch.as_tensor(np.ascontiguousarray(lattice_values), device="cuda")
+    for prec in candidates(dim, p, accuracy):
+        m = Mesh(dim, vertices, elements, eps, mu, p=p, precision=prec, n_rhs=vals.shape[0])
+        t = m.pitch(T, causality_factor)
+        nl = t.info["n_layers"]
+        lb = min(nl - 1, int(window[0] * nl))
+        le = min(nl, max(lb + 1, lb + int(window[1] * nl)))
+        st = m.state_from_lattice(vals)
+        best, ms = t.autotune(st, lb, le)
+        results.append({"precision": prec, "launch": best, "ms": ms[best], "launch_ms": ms})
+    top = min(results, key=lambda r: r["ms"])
+    rec = {"precision": top["precision"], "launch": top["launch"], "launch_name": LAUNCH_NAMES[top["launch"]],
+           "candidates": results}
+    data[key] = rec
+    _save(cache, data)
+    return rec["precision"], rec["launch"], rec
