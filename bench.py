@@ -36,8 +36,8 @@ N_SMS = 152
 # DRAM bytes (read + write) per tent of the FP32 p=4 tent kernel from the last ncu capture of
 # the current kernel version (profiles/tent_layer_kernel_fp32_p4_graded32.md); None once the
 # kernel has changed since the counters were taken.
-TRAFFIC_BYTES_PER_TENT = {"fp32": 27526.0}          # tent_layer_kernel, per tent
-TRAFFIC_PERSISTENT_BYTES = {"fp32": 24425.0}          # tent_persistent_kernel, per tent (full evolve)
+TRAFFIC_BYTES_PER_TENT = {}                           # tent_layer_kernel, per tent
+TRAFFIC_PERSISTENT_BYTES = {}                         # tent_persistent_kernel, per tent (full evolve)
 
 
 def load_peaks():

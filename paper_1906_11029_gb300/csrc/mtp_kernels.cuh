@@ -72,6 +72,7 @@ struct Shape {
     static constexpr int NFB = DIM == 2 ? P + 1 : (P + 1) * (P + 2) / 2;
     static constexpr int NBP = pad4(NB);
     static constexpr int NFBP = pad4(NFB);
+    static constexpr int GIS = pad4(NF);                  // row stride of G^-1 in shared memory
     static constexpr int NV = DIM + 1;
     static constexpr int NT = DIM == 2 ? 128 : 256;   // threads per CTA
     static constexpr int AP = 2;                       // basis functions per thread
@@ -107,7 +108,7 @@ struct SmemLayout {
     using Sh = Shape<DIM, P>;
     static __host__ __device__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
     size_t off_Y, off_Ua, off_Ub, off_tr, off_Gi, off_gphi, off_gdel, off_mat, off_ac, off_gd, off_nrm,
-        off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, off_pair, bytes, state_bytes, tr_bytes;
+        off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, off_pair, off_own, bytes, state_bytes, tr_bytes;
     __host__ __device__ explicit SmemLayout(int mp) {
         size_t o = 0;
         state_bytes = (size_t)mp * Sh::NF * Sh::NBP * sizeof(Real);
@@ -116,7 +117,7 @@ struct SmemLayout {
         off_Ua = o; o = align16(o + state_bytes);
         off_Ub = o; o = align16(o + state_bytes);
         off_tr = o; o = align16(o + tr_bytes);
-        off_Gi = o; o = align16(o + (size_t)mp * Sh::NF * Sh::NF * sizeof(Real));
+        off_Gi = o; o = align16(o + (size_t)mp * Sh::NF * Sh::GIS * sizeof(Real));
         off_gphi = o; o = align16(o + (size_t)mp * 3 * sizeof(double));
         off_gdel = o; o = align16(o + (size_t)mp * 3 * sizeof(double));
         off_mat = o; o = align16(o + (size_t)mp * 2 * sizeof(double));
@@ -130,6 +131,7 @@ struct SmemLayout {
         off_nslot = o; o = align16(o + (size_t)mp * DIM);
         off_nfi = o; o = align16(o + (size_t)mp * DIM);
         off_pair = o; o = align16(o + (size_t)mp * 2 + 4);
+        off_own = o; o = align16(o + (size_t)mp * DIM * 2 + 4);
         bytes = o;
     }
 };
@@ -194,7 +196,9 @@ struct TentCtx {
     double *sGphi, *sGdel, *sMat;
     Real *sAc, *sGd, *sNrm, *sLiftc, *sTrs, *sZ;
     int8_t *sJ, *sNslot, *sNfi, *sPair;   // sPair: [pair][2] element slots (second -1: single)
+    int8_t* sOwn;                         // [facet][2]: (slot, facet position) owning each facet
     int* sNpair;
+    int* sNown;
     int V, ns;
     int64_t pb;
     double tb, dt;
@@ -219,6 +223,8 @@ struct TentCtx {
         sNfi = (int8_t*)(smem + lay.off_nfi);
         sPair = (int8_t*)(smem + lay.off_pair + 4);
         sNpair = (int*)(smem + lay.off_pair);
+        sOwn = (int8_t*)(smem + lay.off_own + 4);
+        sNown = (int*)(smem + lay.off_own);
     }
 };
 
@@ -309,6 +315,17 @@ __device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t ten
             k += pair ? 2 : 1;
         }
         *c.sNpair = np;
+        int no = 0;   // facets containing V, each once: boundary facets and the lower slot of interior ones
+        for (int k = 0; k < ns; ++k)
+            for (int fi = 0; fi < DIM; ++fi) {
+                const int s2 = c.sNslot[k * DIM + fi];
+                if (s2 < 0 || s2 > k) {
+                    c.sOwn[2 * no] = (int8_t)k;
+                    c.sOwn[2 * no + 1] = (int8_t)fi;
+                    ++no;
+                }
+            }
+        *c.sNown = no;
     }
     __syncthreads();
 }
@@ -333,7 +350,7 @@ __device__ void tent_ginv(TentCtx<Real, DIM, P>& c, const KArgs& a, int i) {
             double w[6] = {0, 0, 0, 0, 0, 0}, o[6];
             w[field6<DIM>(s)] = 1.0;
             ginv_apply(w, g, eps, mu, o);
-            for (int r = 0; r < NF; ++r) c.sGi[(k * NF + r) * NF + s] = (Real)o[field6<DIM>(r)];
+            for (int r = 0; r < NF; ++r) c.sGi[(k * NF + r) * Sh::GIS + s] = (Real)o[field6<DIM>(r)];
         }
     }
 }
@@ -342,10 +359,10 @@ __device__ void tent_ginv(TentCtx<Real, DIM, P>& c, const KArgs& a, int i) {
 template <typename Real, int DIM, int P>
 __device__ void tent_apply_ginv(TentCtx<Real, DIM, P>& c, const Real* src, Real* dst) {
     using Sh = Shape<DIM, P>;
-    constexpr int NF = Sh::NF, NB = Sh::NB, NT = Sh::NT, ESZ = NF * Sh::NBP, NBP = Sh::NBP;
-    for (int idx = threadIdx.x; idx < c.ns * NB; idx += NT) {
+    constexpr int NF = Sh::NF, NB = Sh::NB, ESZ = NF * Sh::NBP, NBP = Sh::NBP, GIS = Sh::GIS;
+    for (int idx = threadIdx.x; idx < c.ns * NB; idx += blockDim.x) {
         const int k = idx / NB, b = idx - k * NB;
-        const Real* Gi = c.sGi + k * NF * NF;
+        const Real* Gi = c.sGi + k * NF * GIS;
         Real y[NF];
 #pragma unroll
         for (int s = 0; s < NF; ++s) y[s] = src[k * ESZ + s * NBP + b];
@@ -353,7 +370,7 @@ __device__ void tent_apply_ginv(TentCtx<Real, DIM, P>& c, const Real* src, Real*
         for (int r = 0; r < NF; ++r) {
             Real acc = 0;
 #pragma unroll
-            for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * y[s];
+            for (int s = 0; s < NF; ++s) acc += Gi[r * GIS + s] * y[s];
             dst[k * ESZ + r * NBP + b] = acc;
         }
     }
@@ -426,10 +443,11 @@ template <typename Real, int DIM, int P>
 __device__ void tent_fluxes(TentCtx<Real, DIM, P>& c, Real* tr) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NFB = Sh::NFB, NT = Sh::NT, NFBP = Sh::NFBP, TSZ = DIM * NF * NFBP;
-    for (int idx = threadIdx.x; idx < c.ns * DIM * NFB; idx += NT) {
-        const int k = idx / (DIM * NFB), rem = idx - k * DIM * NFB, fi = rem / NFB, cc = rem - fi * NFB;
+    const int nown = *c.sNown;
+    for (int idx = threadIdx.x; idx < nown * NFB; idx += blockDim.x) {
+        const int oi = idx / NFB, cc = idx - oi * NFB;
+        const int k = c.sOwn[2 * oi], fi = c.sOwn[2 * oi + 1];
         const int s2 = c.sNslot[k * DIM + fi];
-        if (s2 >= 0 && s2 < k) continue;
         Real* mine = tr + k * TSZ + fi * NF * NFBP + cc;
         Real um[6] = {0, 0, 0, 0, 0, 0}, up[6] = {0, 0, 0, 0, 0, 0}, F[6], nrm[3];
 #pragma unroll
@@ -600,7 +618,7 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
             const int k = kk[e];
             const Real* U = Ucur + k * ESZ;
             const Real* gd = c.sGd + 3 * k;
-            const Real* Gi = c.sGi + k * NF * NF;
+            const Real* Gi = c.sGi + k * NF * Sh::GIS;
 #pragma unroll
             for (int ai = 0; ai < AP; ++ai) {
                 if (ai == 1 && !two) break;
@@ -628,9 +646,12 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
                     }
 #pragma unroll
                     for (int r = 0; r < NF; ++r) {
+                        Real gr[Sh::GIS];
+#pragma unroll
+                        for (int q = 0; q < Sh::GIS; q += W) Vec<Real>::get(*(const VT*)(Gi + r * Sh::GIS + q), gr + q);
                         Real acc = 0;
 #pragma unroll
-                        for (int s = 0; s < NF; ++s) acc += Gi[r * NF + s] * r6[s];
+                        for (int s = 0; s < NF; ++s) acc += gr[s] * r6[s];
                         Unext[k * ESZ + r * NBP + av] = acc;
                     }
                 }
@@ -1028,7 +1049,7 @@ __device__ void tent_stage_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, c
             const float* ac = c.sAc + k * DIM * 3;
             const float* U = Ucur + k * ESZ;
             const float* gd = c.sGd + 3 * k;
-            const float* Gi = c.sGi + k * NF * NF;
+            const float* Gi = c.sGi + k * NF * Sh::GIS;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int av = 16 * mt + g + 8 * h;
@@ -1081,7 +1102,7 @@ __device__ void tent_stage_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, c
                             const int r = 2 * t + q;
                             float acc = 0;
 #pragma unroll
-                            for (int s = 0; s < 6; ++s) acc += Gi[r * NF + s] * r6[s];
+                            for (int s = 0; s < 6; ++s) acc += Gi[r * Sh::GIS + s] * r6[s];
                             Unext[k * ESZ + r * NBP + av] = acc;
                         }
                     }
