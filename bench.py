@@ -33,9 +33,9 @@ import numpy as np  # noqa: E402
 
 FP32_SM_LANES = 128            # FP32 FMA lanes per SM (Blackwell)
 N_SMS = 152
-# DRAM bytes (read + write) per tent of the FP32 p=4 tent kernel from the last ncu capture of
-# the current kernel version (profiles/tent_layer_kernel_fp32_p4_graded32.md); None once the
-# kernel has changed since the counters were taken.
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per tent of the FP32 p=4 tent
+# kernels on the graded 32^3 workload, from the last ncu capture of the current kernel
+# version; an entry is removed once its kernel has changed since the counters were taken.
 TRAFFIC_BYTES_PER_TENT = {}                           # tent_layer_kernel, per tent
 TRAFFIC_PERSISTENT_BYTES = {}                         # tent_persistent_kernel, per tent (full evolve)
 
@@ -193,15 +193,17 @@ def run_profile(args):
     a, b = (int(x) for x in args.profile_window.split(":"))
     w = make_workload(args.workload)
     prec = mtp.MTP_FP32 if args.precision == "fp32" else mtp.MTP_FP64
-    mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=prec)
+    flags = mtp.MTP_FLAG_LAYER_LAUNCHES if args.layer_launches else 0
+    mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=prec, flags=flags)
     tents = mesh.pitch(w.T, w.causality)
     state = mesh.state_from_lattice(torch.tensor(initial_lattice(w)[None], device="cuda"))
     if a > 0:
         tents.evolve_layers(state, 0, a)
     tents.evolve_layers(state, a, b)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_window": [a, b], "launches": int(np.count_nonzero(
-        np.diff(tents.get()["layer_ptr"][a:b + 1]))), "workload": w.name}))
+    launches = int(np.count_nonzero(np.diff(tents.get()["layer_ptr"][a:b + 1]))) if args.layer_launches else 1
+    print(json.dumps({"profile_window": [a, b], "launches": launches, "workload": w.name,
+                      "kernel": "tent_layer_kernel" if args.layer_launches else "tent_persistent_kernel"}))
 
 
 def run_profile_evolve(args):

@@ -31,6 +31,9 @@ struct DeviceMesh {
     void* S = nullptr;
     void* Tr = nullptr;
     void* L = nullptr;
+    void* Sc = nullptr;           // thread-major copies of S, Tr, L for the SIMT tent kernels
+    void* Trc = nullptr;
+    void* Lc = nullptr;
     double* V = nullptr;
     double* Vinv = nullptr;
     float* Sf = nullptr;          // tensor-core fragment tables (TF32 modes)
@@ -86,6 +89,26 @@ static std::vector<double> pad_rows(const std::vector<double>& src, int cols) {
     std::vector<double> out(rows * pc, 0.0);
     for (size_t r = 0; r < rows; ++r)
         for (int c = 0; c < cols; ++c) out[r * pc + c] = src[r * cols + c];
+    return out;
+}
+
+// Thread-major layout of `nmat` row-major rows x cols matrices for the SIMT tent kernels.
+// A thread owns a group of `ap` consecutive rows and reads, per step, `w` consecutive
+// columns of each of them as one 16-byte vector; consecutive threads own consecutive row
+// groups.  Entry (r, c) of matrix mt goes to
+//   [mt][c / w][r % ap][r / ap][c % w]   (columns padded to pad4(cols), rows to the groups)
+// so that the vectors that the lanes of a warp read for one (matrix, column block, row of
+// the group) are contiguous in memory.
+static std::vector<double> thread_major(const std::vector<double>& src, int nmat, int rows, int cols, int w,
+                                        int ap) {
+    const int nch = pad4(cols) / w, nrg = (rows + ap - 1) / ap;
+    const size_t msz = (size_t)nch * ap * nrg * w;
+    std::vector<double> out(nmat * msz, 0.0);
+    for (int mt = 0; mt < nmat; ++mt)
+        for (int r = 0; r < rows; ++r)
+            for (int c = 0; c < cols; ++c)
+                out[mt * msz + (((size_t)(c / w) * ap + r % ap) * nrg + r / ap) * w + c % w] =
+                    src[((size_t)mt * rows + r) * cols + c];
     return out;
 }
 
@@ -148,6 +171,12 @@ int device_mesh_upload(Mesh& m) {
     MTP_TRY(upload_real(m, &d.S, pad_rows(m.ref.S, m.nb)));     // [j][l][a][NBP]
     MTP_TRY(upload_real(m, &d.Tr, pad_rows(m.ref.Tr, m.nb)));   // [f][c][NBP]
     MTP_TRY(upload_real(m, &d.L, pad_rows(m.ref.L, m.nfb)));    // [j][f][a][NFBP]
+    {
+        const int w = m.precision == MTP_FP64 ? 2 : 4, ap = 2, nv = m.dim + 1;
+        MTP_TRY(upload_real(m, &d.Sc, thread_major(m.ref.S, nv * m.dim, m.nb, m.nb, w, ap)));
+        MTP_TRY(upload_real(m, &d.Trc, thread_major(m.ref.Tr, nv, m.nfb, m.nb, w, ap)));
+        MTP_TRY(upload_real(m, &d.Lc, thread_major(m.ref.L, nv * nv, m.nb, m.nfb, w, ap)));
+    }
     if (m.precision == MTP_TF32 || m.precision == MTP_TF32X3) {
         const RefTables& r = m.ref;
         const int nb = m.nb, nfb = m.nfb, d3 = m.dim, nvx = m.dim + 1;
@@ -183,7 +212,8 @@ int device_mesh_upload(Mesh& m) {
 void device_mesh_free(Mesh& m) {
     if (!m.dev) return;
     DeviceMesh& d = *m.dev;
-    void* ptrs[] = {d.geo, d.elems, d.patch_ptr, d.patch_elem, d.patch_info, d.S, d.Tr, d.L, d.V, d.Vinv, d.partial,
+    void* ptrs[] = {d.geo, d.elems, d.patch_ptr, d.patch_elem, d.patch_info, d.S, d.Tr, d.L, d.Sc, d.Trc, d.Lc,
+                    d.V, d.Vinv, d.partial,
                     d.Sf, d.Lfr, d.Trf, d.Sf_lo, d.Lfr_lo, d.Trf_lo};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -406,6 +436,9 @@ static void fill_args(Tents& t, void* state, KArgs& a) {
     a.S = dm.S;
     a.Tr = dm.Tr;
     a.L = dm.L;
+    a.Sc = dm.Sc;
+    a.Trc = dm.Trc;
+    a.Lc = dm.Lc;
     a.Sf = (const float4*)dm.Sf;
     a.Lfr = (const float4*)dm.Lfr;
     a.Trf = (const float4*)dm.Trf;

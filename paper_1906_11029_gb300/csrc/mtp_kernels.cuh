@@ -47,6 +47,11 @@ struct KArgs {
     const void* S;              // [j][l][a][NBP]  reference tables in the state precision,
     const void* Tr;             // [f][c][NBP]     rows padded with zeros (see pad4)
     const void* L;              // [j][f][a][NFBP]
+    // the same tables thread-major (rows grouped by AP, see Shape): entry (r, c) of one
+    // matrix at [c / W][r % AP][r / AP][c % W], W = elements per 16-byte vector
+    const void* Sc;             // matrices (j, l), NB x NB
+    const void* Trc;            // matrices f, NFB x NB
+    const void* Lc;             // matrices (j, f), NB x NFB
     // tensor-core modes: A-operand tables in m16n8k8 fragment order (32 lanes x 4 TF32 values
     // per fragment), hi part and (split mode) lo part
     const float4* Sf;           // [j][l][mt][kt]
@@ -384,19 +389,19 @@ __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real
     using VT = typename Vec<Real>::T;
     constexpr int NF = Sh::NF, NFB = Sh::NFB, NT = Sh::NT, NBP = Sh::NBP, NFBP = Sh::NFBP;
     constexpr int AP = Sh::AP, NCG = Sh::NCG, W = Vec<Real>::W, ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
-    const Real* Tr = (const Real*)a.Tr;
+    constexpr int TMAT = NBP * AP * NCG;   // one thread-major facet table
+    const Real* Tr = (const Real*)a.Trc;
     for (int idx = threadIdx.x; idx < c.ns * NCG; idx += NT) {
         const int k = idx / NCG;
-        const int c0 = (idx - k * NCG) * AP;
+        const int cg = idx - k * NCG, c0 = cg * AP;
         const bool two = c0 + 1 < NFB;
         const int j = c.sJ[k];
         const Real* U = Ucur + k * ESZ;
-        const Real* T[DIM][AP];
+        const Real* T[DIM];
 #pragma unroll
         for (int fi = 0; fi < DIM; ++fi) {
             const int f = fi + (fi >= j ? 1 : 0);
-            T[fi][0] = Tr + ((size_t)f * NFB + c0) * NBP;
-            T[fi][1] = two ? T[fi][0] + NBP : T[fi][0];
+            T[fi] = Tr + (size_t)f * TMAT + cg * W;
         }
         Real acc[DIM][AP][NF];
 #pragma unroll
@@ -411,7 +416,8 @@ __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real
 #pragma unroll
             for (int fi = 0; fi < DIM; ++fi)
 #pragma unroll
-                for (int ci = 0; ci < AP; ++ci) Vec<Real>::get(__ldg((const VT*)(T[fi][ci] + b)), tv[fi][ci]);
+                for (int ci = 0; ci < AP; ++ci)
+                    Vec<Real>::get(__ldg((const VT*)(T[fi] + b * AP * NCG + ci * NCG * W)), tv[fi][ci]);
 #pragma unroll
             for (int s = 0; s < NF; ++s) {
                 Real u[W];
@@ -486,13 +492,14 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
     constexpr int NF = Sh::NF, NB = Sh::NB, NV = Sh::NV, NT = Sh::NT, NBP = Sh::NBP, NFBP = Sh::NFBP;
     constexpr int AP = Sh::AP, NAG = Sh::NAG, W = Vec<Real>::W, ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
     constexpr int EP = sizeof(Real) == 4 ? 2 : 1;   // elements per thread (FP64: register budget)
-    const Real* S = (const Real*)a.S;
-    const Real* Lf = (const Real*)a.L;
+    constexpr int SMAT = NBP * AP * NAG, LMAT = NFBP * AP * NAG;   // thread-major S and L matrices
+    const Real* S = (const Real*)a.Sc;
+    const Real* Lf = (const Real*)a.Lc;
     const Real cn = (Real)a.taylor[n];
     const Real nn = (Real)n;
     const int nitems = EP == 2 ? *c.sNpair : c.ns;   // pairs, or single elements
     for (int idx = threadIdx.x; idx < nitems * NAG; idx += NT) {
-        const int pi = idx / NAG, a0 = (idx - pi * NAG) * AP;
+        const int pi = idx / NAG, ag = idx - pi * NAG, a0 = ag * AP;
         const bool two = a0 + 1 < NB;
         const int k0 = EP == 2 ? c.sPair[2 * pi] : pi;
         const int kk1 = EP == 2 ? c.sPair[2 * pi + 1] : -1;
@@ -510,16 +517,16 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
                     for (int l = 0; l < DIM; ++l)
 #pragma unroll
                         for (int s = 0; s < NF; ++s) Pm[e][ai][l][s] = 0;
-            const Real* S0 = S + ((size_t)j * DIM * NB + a0) * NBP;
-            const Real* S1 = two ? S0 + NBP : S0;
+            const Real* Sg = S + (size_t)j * DIM * SMAT + ag * W;
 #pragma unroll 1
             for (int b = 0; b < NBP; b += W) {
                 Real sv[AP][DIM][W];
+                const Real* Sb = Sg + b * AP * NAG;
 #pragma unroll
-                for (int l = 0; l < DIM; ++l) {
-                    Vec<Real>::get(__ldg((const VT*)(S0 + (size_t)l * NB * NBP + b)), sv[0][l]);
-                    Vec<Real>::get(__ldg((const VT*)(S1 + (size_t)l * NB * NBP + b)), sv[1][l]);
-                }
+                for (int l = 0; l < DIM; ++l)
+#pragma unroll
+                    for (int ai = 0; ai < AP; ++ai)
+                        Vec<Real>::get(__ldg((const VT*)(Sb + l * SMAT + ai * NAG * W)), sv[ai][l]);
 #pragma unroll
                 for (int e = 0; e < EP; ++e) {
                     const Real* U = Ucur + kk[e] * ESZ;
@@ -576,8 +583,7 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
 #pragma unroll
         for (int fi = 0; fi < DIM; ++fi) {
             const int f = fi + (fi >= j ? 1 : 0);
-            const Real* L0 = Lf + (((size_t)j * NV + f) * NB + a0) * NFBP;
-            const Real* L1 = two ? L0 + NFBP : L0;
+            const Real* Lg = Lf + ((size_t)j * NV + f) * LMAT + ag * W;
             Real acc[EP][AP][NF];
 #pragma unroll
             for (int e = 0; e < EP; ++e)
@@ -588,8 +594,8 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
 #pragma unroll
             for (int cc = 0; cc < NFBP; cc += W) {
                 Real l0[W], l1[W];
-                Vec<Real>::get(__ldg((const VT*)(L0 + cc)), l0);
-                Vec<Real>::get(__ldg((const VT*)(L1 + cc)), l1);
+                Vec<Real>::get(__ldg((const VT*)(Lg + cc * AP * NAG)), l0);
+                Vec<Real>::get(__ldg((const VT*)(Lg + cc * AP * NAG + NAG * W)), l1);
 #pragma unroll
                 for (int e = 0; e < EP; ++e) {
                     const Real* Fx = tr + kk[e] * TSZ + fi * NF * NFBP;
