@@ -93,12 +93,12 @@ static std::vector<double> pad_rows(const std::vector<double>& src, int cols) {
 }
 
 // Thread-major layout of `nmat` row-major rows x cols matrices for the SIMT tent kernels.
-// A thread owns a group of `ap` consecutive rows and reads, per step, `w` consecutive
-// columns of each of them as one 16-byte vector; consecutive threads own consecutive row
-// groups.  Entry (r, c) of matrix mt goes to
-//   [mt][c / w][r % ap][r / ap][c % w]   (columns padded to pad4(cols), rows to the groups)
+// With nrg = ceil(rows / ap) row groups, a thread owns rows g, g + nrg, ..., and reads, per
+// step, `w` consecutive columns of each of them as one 16-byte vector; consecutive threads
+// own consecutive groups.  Entry (r, c) of matrix mt goes to
+//   [mt][c / w][r / nrg][r % nrg][c % w]   (columns padded to pad4(cols), rows to ap * nrg)
 // so that the vectors that the lanes of a warp read for one (matrix, column block, row of
-// the group) are contiguous in memory.
+// the group) are contiguous in memory, and the rows the lanes write are consecutive.
 static std::vector<double> thread_major(const std::vector<double>& src, int nmat, int rows, int cols, int w,
                                         int ap) {
     const int nch = pad4(cols) / w, nrg = (rows + ap - 1) / ap;
@@ -107,7 +107,7 @@ static std::vector<double> thread_major(const std::vector<double>& src, int nmat
     for (int mt = 0; mt < nmat; ++mt)
         for (int r = 0; r < rows; ++r)
             for (int c = 0; c < cols; ++c)
-                out[mt * msz + (((size_t)(c / w) * ap + r % ap) * nrg + r / ap) * w + c % w] =
+                out[mt * msz + (((size_t)(c / w) * ap + r / nrg) * nrg + r % nrg) * w + c % w] =
                     src[((size_t)mt * rows + r) * cols + c];
     return out;
 }

@@ -47,8 +47,9 @@ struct KArgs {
     const void* S;              // [j][l][a][NBP]  reference tables in the state precision,
     const void* Tr;             // [f][c][NBP]     rows padded with zeros (see pad4)
     const void* L;              // [j][f][a][NFBP]
-    // the same tables thread-major (rows grouped by AP, see Shape): entry (r, c) of one
-    // matrix at [c / W][r % AP][r / AP][c % W], W = elements per 16-byte vector
+    // the same tables thread-major: with G = ceil(rows / AP) row groups (NAG or NCG, see
+    // Shape), entry (r, c) of one matrix at [c / W][r / G][r % G][c % W], W = elements per
+    // 16-byte vector; a thread owns rows g and g + G
     const void* Sc;             // matrices (j, l), NB x NB
     const void* Trc;            // matrices f, NFB x NB
     const void* Lc;             // matrices (j, f), NB x NFB
@@ -168,23 +169,6 @@ __device__ __forceinline__ void upwind6(const Real um[6], const Real up[6], cons
     out[3] = -(et[1] * n[2] - et[2] * n[1]);
     out[4] = -(et[2] * n[0] - et[0] * n[2]);
     out[5] = -(et[0] * n[1] - et[1] * n[0]);
-}
-
-// closed-form inverse of G(g) u = (eps E - H x g, mu H + E x g) (Sec. 4), FP64
-__device__ __forceinline__ void ginv_apply(const double w[6], const double g[3], double eps, double mu,
-                                           double out[6]) {
-    const double em = eps * mu;
-    const double s = 1.0 / (em - (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
-    double a[3] = {mu * w[0] + (w[4] * g[2] - w[5] * g[1]), mu * w[1] + (w[5] * g[0] - w[3] * g[2]),
-                   mu * w[2] + (w[3] * g[1] - w[4] * g[0])};
-    double b[3] = {eps * w[3] - (w[1] * g[2] - w[2] * g[1]), eps * w[4] - (w[2] * g[0] - w[0] * g[2]),
-                   eps * w[5] - (w[0] * g[1] - w[1] * g[0])};
-    const double ga = (g[0] * a[0] + g[1] * a[1] + g[2] * a[2]) / em;
-    const double gb = (g[0] * b[0] + g[1] * b[1] + g[2] * b[2]) / em;
-    for (int c = 0; c < 3; ++c) {
-        out[c] = s * (a[c] - g[c] * ga);
-        out[3 + c] = s * (b[c] - g[c] * gb);
-    }
 }
 
 template <int DIM>
@@ -335,28 +319,55 @@ __device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t ten
     __syncthreads();
 }
 
-// G(t_i)^-1 per element, built in FP64 from the closed form, stored in the state precision.
+// G(t_i)^-1 per element from the closed form (Sec. 4): with P = I - g g^T / (eps mu) and
+// s = 1 / (eps mu - |g|^2),  G^-1 = s [[mu P, -[g]x], [[g]x, eps P]]  ([g]x w = g x w),
+// one row per thread, in the state precision.  The causality test |g| < sqrt(eps mu) at
+// t_i (and at the tent top when i = 0) decides an error and is taken in FP64.
 template <typename Real, int DIM, int P>
 __device__ void tent_ginv(TentCtx<Real, DIM, P>& c, const KArgs& a, int i) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NT = Sh::NT;
     const double ti = (double)i / (double)a.m;
     for (int k = threadIdx.x; k < c.ns; k += NT) {
-        double g[3];
-        for (int q = 0; q < 3; ++q) g[q] = c.sGphi[3 * k + q] + ti * c.sGdel[3 * k + q];
         const double eps = c.sMat[2 * k], mu = c.sMat[2 * k + 1];
-        if (!(g[0] * g[0] + g[1] * g[1] + g[2] * g[2] < eps * mu)) atomicCAS(a.err, 0, 1);
+        double gg = 0;
+        for (int q = 0; q < 3; ++q) {
+            const double g = c.sGphi[3 * k + q] + ti * c.sGdel[3 * k + q];
+            gg += g * g;
+        }
+        if (!(gg < eps * mu)) atomicCAS(a.err, 0, 1);
         if (i == 0) {   // grad phi is affine in t, so bottom and top bound the whole tent
-            double gt[3];
-            for (int q = 0; q < 3; ++q) gt[q] = c.sGphi[3 * k + q] + c.sGdel[3 * k + q];
-            if (!(gt[0] * gt[0] + gt[1] * gt[1] + gt[2] * gt[2] < eps * mu)) atomicCAS(a.err, 0, 1);
+            double gt = 0;
+            for (int q = 0; q < 3; ++q) {
+                const double g = c.sGphi[3 * k + q] + c.sGdel[3 * k + q];
+                gt += g * g;
+            }
+            if (!(gt < eps * mu)) atomicCAS(a.err, 0, 1);
         }
-        for (int s = 0; s < NF; ++s) {
-            double w[6] = {0, 0, 0, 0, 0, 0}, o[6];
-            w[field6<DIM>(s)] = 1.0;
-            ginv_apply(w, g, eps, mu, o);
-            for (int r = 0; r < NF; ++r) c.sGi[(k * NF + r) * Sh::GIS + s] = (Real)o[field6<DIM>(r)];
+    }
+    const Real tr = (Real)ti;
+    for (int idx = threadIdx.x; idx < c.ns * NF; idx += NT) {
+        const int k = idx / NF, R = field6<DIM>(idx - k * NF);
+        Real g[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) g[q] = (Real)c.sGphi[3 * k + q] + tr * (Real)c.sGdel[3 * k + q];
+        const Real eps = (Real)c.sMat[2 * k], mu = (Real)c.sMat[2 * k + 1], em = eps * mu;
+        const Real s = Real(1) / (em - (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
+        const int rq = R < 3 ? R : R - 3;                  // component of the row's field
+        const Real d = s * (R < 3 ? mu : eps);             // diagonal block: s mu P or s eps P
+        const Real pr = d * g[rq] / em;
+        const Real sx = R < 3 ? -s : s;                    // off-diagonal block: -s [g]x or s [g]x
+        Real row[6];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const Real cr = q == rq ? Real(0) : ((q == (rq + 1) % 3) ? -g[(rq + 2) % 3] : g[(rq + 1) % 3]);
+            const Real diag = (q == rq ? d : Real(0)) - pr * g[q];
+            row[R < 3 ? q : 3 + q] = diag;
+            row[R < 3 ? 3 + q : q] = sx * cr;
         }
+        Real* out = c.sGi + idx * Sh::GIS;
+#pragma unroll
+        for (int q = 0; q < NF; ++q) out[q] = row[field6<DIM>(q)];
     }
 }
 
@@ -393,8 +404,8 @@ __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real
     const Real* Tr = (const Real*)a.Trc;
     for (int idx = threadIdx.x; idx < c.ns * NCG; idx += NT) {
         const int k = idx / NCG;
-        const int cg = idx - k * NCG, c0 = cg * AP;
-        const bool two = c0 + 1 < NFB;
+        const int cg = idx - k * NCG;     // facet modes cg and cg + NCG
+        const bool two = cg + NCG < NFB;
         const int j = c.sJ[k];
         const Real* U = Ucur + k * ESZ;
         const Real* T[DIM];
@@ -433,11 +444,11 @@ __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real
         const Real sc = c.sTrs[k];
 #pragma unroll
         for (int fi = 0; fi < DIM; ++fi) {
-            Real* out = tr + k * TSZ + fi * NF * NFBP + c0;
+            Real* out = tr + k * TSZ + fi * NF * NFBP + cg;
 #pragma unroll
             for (int s = 0; s < NF; ++s) {
                 out[s * NFBP] = acc[fi][0][s] * sc;
-                if (two) out[s * NFBP + 1] = acc[fi][1][s] * sc;
+                if (two) out[s * NFBP + NCG] = acc[fi][1][s] * sc;
             }
         }
     }
@@ -499,8 +510,8 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
     const Real nn = (Real)n;
     const int nitems = EP == 2 ? *c.sNpair : c.ns;   // pairs, or single elements
     for (int idx = threadIdx.x; idx < nitems * NAG; idx += NT) {
-        const int pi = idx / NAG, ag = idx - pi * NAG, a0 = ag * AP;
-        const bool two = a0 + 1 < NB;
+        const int pi = idx / NAG, ag = idx - pi * NAG;   // basis functions ag and ag + NAG
+        const bool two = ag + NAG < NB;
         const int k0 = EP == 2 ? c.sPair[2 * pi] : pi;
         const int kk1 = EP == 2 ? c.sPair[2 * pi + 1] : -1;
         const bool has1 = kk1 >= 0;
@@ -628,7 +639,7 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
 #pragma unroll
             for (int ai = 0; ai < AP; ++ai) {
                 if (ai == 1 && !two) break;
-                const int av = a0 + ai;
+                const int av = ag + ai * NAG;
 #pragma unroll
                 for (int s = 0; s < NF; ++s) c.sY[k * ESZ + s * NBP + av] += cn * Yn[e][ai][s];
                 if (n < a.q) {
