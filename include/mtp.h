@@ -106,6 +106,18 @@ int mtp_mesh_info(mtp_mesh_t mesh, int* dim, int* n_fields, int* n_basis,
  * (layer, vertex). */
 int mtp_pitch_tents(mtp_mesh_t mesh, const double* wavespeed, double causality_factor,
                     double T, mtp_tents_t* out);
+
+/* The same pitcher with its rounds on the current CUDA device (Sec. 2: tents at vertices
+ * that are not neighbours are pitched independently, so each round is one parallel step).
+ * Same rule, arguments and errors as mtp_pitch_tents, and the same tent list bit for bit
+ * (identical FP64 operations; each round's tents are emitted in vertex order, and a
+ * tent's layer equals its round, so the list comes out sorted by (layer, vertex)).
+ * The per-edge bounds are computed on the host as in mtp_pitch_tents; the rounds run on
+ * `stream`, and the call returns when the tent list is on the host.  Device memory: about
+ * 70 bytes per vertex plus 24 bytes per tent of output, allocated and freed inside the
+ * call.  MTP_ECUDA / MTP_ENOMEM on CUDA failures. */
+int mtp_pitch_tents_device(mtp_mesh_t mesh, const double* wavespeed, double causality_factor,
+                           double T, mtp_tents_t* out, void* stream);
 void mtp_tents_destroy(mtp_tents_t tents);
 
 /* n_tents, n_layers, and the spacetime DOF count of one evolve (Sec. 5.2):

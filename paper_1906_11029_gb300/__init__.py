@@ -26,7 +26,7 @@ MTP_FLAG_LAYER_LAUNCHES, MTP_FLAG_TEST_STALL = 1, 2
 _CODES = {0: "MTP_OK", -1: "MTP_EINVAL", -2: "MTP_EMESH", -3: "MTP_ECAUSAL", -4: "MTP_ENOMEM",
           -5: "MTP_ECUDA", -6: "MTP_ETIMEOUT", -7: "MTP_ENUMERIC", -8: "MTP_EUNSUPPORTED"}
 
-ABI_SYMBOLS = ["mtp_mesh_create", "mtp_mesh_destroy", "mtp_mesh_info", "mtp_pitch_tents",
+ABI_SYMBOLS = ["mtp_mesh_create", "mtp_mesh_destroy", "mtp_mesh_info", "mtp_pitch_tents", "mtp_pitch_tents_device",
                "mtp_tents_destroy", "mtp_tents_info", "mtp_tents_get", "mtp_state_from_lattice",
                "mtp_state_to_lattice", "mtp_evolve", "mtp_evolve_layers", "mtp_evolve_host",
                "mtp_tents_set_launch", "mtp_tents_autotune", "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_info", "mtp_batch_evolve",
@@ -55,6 +55,7 @@ def _load():
         "mtp_mesh_destroy": (None, [P]),
         "mtp_mesh_info": (C.c_int, [P, P, P, P, P, P, P]),
         "mtp_pitch_tents": (C.c_int, [P, P, D, D, C.POINTER(P)]),
+        "mtp_pitch_tents_device": (C.c_int, [P, P, D, D, C.POINTER(P), P]),
         "mtp_tents_destroy": (None, [P]),
         "mtp_tents_info": (C.c_int, [P, P, P, P]),
         "mtp_tents_get": (C.c_int, [P, P, P, P, P, P]),
@@ -141,6 +142,14 @@ def mtp_pitch_tents(mesh, T, causality_factor=0.5, wavespeed=None):
     ws = None if wavespeed is None else np.ascontiguousarray(wavespeed, np.float64)
     h = C.c_void_p()
     _check(_lib.mtp_pitch_tents(mesh, _ptr(ws), causality_factor, T, C.byref(h)))
+    return h
+
+
+def mtp_pitch_tents_device(mesh, T, causality_factor=0.5, wavespeed=None, stream=None):
+    """Same tent list as mtp_pitch_tents, with the rounds on the current CUDA device."""
+    ws = None if wavespeed is None else np.ascontiguousarray(wavespeed, np.float64)
+    h = C.c_void_p()
+    _check(_lib.mtp_pitch_tents_device(mesh, _ptr(ws), causality_factor, T, C.byref(h), _stream(stream)))
     return h
 
 
@@ -305,8 +314,9 @@ class Mesh:
     def energy(self, state_dev, stream=None):
         return mtp_energy(self.h, state_dev, self.n_rhs, stream)
 
-    def pitch(self, T, causality_factor=0.5, wavespeed=None):
-        return Tents(self, T, causality_factor, wavespeed)
+    def pitch(self, T, causality_factor=0.5, wavespeed=None, device=False):
+        """Tents to time T; ``device=True`` runs the pitcher's rounds on the GPU (same list)."""
+        return Tents(self, T, causality_factor, wavespeed, device)
 
     def __del__(self):
         if getattr(self, "h", None):
@@ -315,10 +325,11 @@ class Mesh:
 
 
 class Tents:
-    def __init__(self, mesh: Mesh, T, causality_factor=0.5, wavespeed=None):
+    def __init__(self, mesh: Mesh, T, causality_factor=0.5, wavespeed=None, device=False):
         self.mesh = mesh                       # keeps the mesh alive
         self.T = T
-        self.h = mtp_pitch_tents(mesh.h, T, causality_factor, wavespeed)
+        pitch = mtp_pitch_tents_device if device else mtp_pitch_tents
+        self.h = pitch(mesh.h, T, causality_factor, wavespeed)
         self.info = mtp_tents_info(self.h)
 
     def get(self):

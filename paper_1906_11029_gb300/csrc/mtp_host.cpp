@@ -251,7 +251,7 @@ static int build_mesh(int dim, int64_t nv, const double* X, int64_t ne, const in
 // ---------------------------------------------------------------------------------
 // pitcher (see mtp_pitch_tents in mtp.h for the rule)
 // ---------------------------------------------------------------------------------
-int pitch(const Mesh& m, const double* wavespeed, double cf, double T, Tents& out) {
+int pitch_graph(const Mesh& m, const double* wavespeed, double cf, PitchGraph& g) {
     const int d = m.dim, nvert = d + 1;
     const int64_t nv = m.nv, ne = m.ne;
     std::vector<double> k(nv, INFINITY), c(ne);
@@ -311,7 +311,8 @@ int pitch(const Mesh& m, const double* wavespeed, double cf, double T, Tents& ou
             for (int j = i + 1; j < nvert; ++j) ekeys.emplace_back((int64_t)el[i] * nv + el[j], c[e]);
     }
     std::sort(ekeys.begin(), ekeys.end());
-    std::vector<int64_t> ptr(nv + 1, 0);
+    std::vector<int64_t>& ptr = g.ptr;
+    ptr.assign(nv + 1, 0);
     std::vector<std::pair<int64_t, double>> edges;   // unique, with max c
     for (size_t i = 0; i < ekeys.size();) {
         size_t j = i;
@@ -322,8 +323,10 @@ int pitch(const Mesh& m, const double* wavespeed, double cf, double T, Tents& ou
     }
     for (auto& ed : edges) { ptr[ed.first / nv + 1]++; ptr[ed.first % nv + 1]++; }
     for (int64_t v = 0; v < nv; ++v) ptr[v + 1] += ptr[v];
-    std::vector<int32_t> dst(ptr[nv]);
-    std::vector<double> bnd(ptr[nv]);
+    std::vector<int32_t>& dst = g.dst;
+    std::vector<double>& bnd = g.bnd;
+    dst.assign(ptr[nv], 0);
+    bnd.assign(ptr[nv], 0.0);
     {
         std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
         for (auto& ed : edges) {
@@ -339,6 +342,17 @@ int pitch(const Mesh& m, const double* wavespeed, double cf, double T, Tents& ou
             for (int64_t q = ptr[v]; q < ptr[v + 1]; ++q) { dst[q] = row[q - ptr[v]].first; bnd[q] = row[q - ptr[v]].second; }
         }
     }
+    return MTP_OK;
+}
+
+int pitch(const Mesh& m, const double* wavespeed, double cf, double T, Tents& out) {
+    const int64_t nv = m.nv;
+    PitchGraph g;
+    int rc = pitch_graph(m, wavespeed, cf, g);
+    if (rc != MTP_OK) return rc;
+    const std::vector<int64_t>& ptr = g.ptr;
+    const std::vector<int32_t>& dst = g.dst;
+    const std::vector<double>& bnd = g.bnd;
     // rounds
     std::vector<double> tau(nv, 0.0);
     std::vector<int64_t> last(nv, -1);
@@ -412,15 +426,19 @@ int pitch(const Mesh& m, const double* wavespeed, double cf, double T, Tents& ou
     out.layer_ptr.assign(nl + 1, 0);
     for (size_t i = 0; i < n; ++i) out.layer_ptr[out.layer[i] + 1]++;
     for (int64_t l = 0; l < nl; ++l) out.layer_ptr[l + 1] += out.layer_ptr[l];
+    pitch_finish(m, T, cf, out);
+    return MTP_OK;
+}
+
+void pitch_finish(const Mesh& m, double T, double cf, Tents& out) {
     double dofs = 0;
-    for (size_t i = 0; i < n; ++i) {
+    for (size_t i = 0; i < out.vertex.size(); ++i) {
         int32_t v = out.vertex[i];
         dofs += (double)(m.patch_ptr[v + 1] - m.patch_ptr[v]);
     }
     out.spacetime_dofs = dofs * m.nf * m.nb * (double)m.m * (double)m.q * m.n_rhs;
     out.T = T;
     out.cf = cf;
-    return MTP_OK;
 }
 
 }  // namespace mtp
@@ -498,6 +516,27 @@ int mtp_pitch_tents(mtp_mesh_t mesh, const double* wavespeed, double cf, double 
     h->t.mesh = &mesh->m;
     int rc = pitch(mesh->m, wavespeed, cf, T, h->t);
     if (rc != MTP_OK) return rc;
+    *out = h.release();
+    return MTP_OK;
+    MTP_GUARD_END
+}
+
+int mtp_pitch_tents_device(mtp_mesh_t mesh, const double* wavespeed, double cf, double T, mtp_tents_t* out,
+                           void* stream) {
+    MTP_GUARD_BEGIN
+    if (!out) return set_error(MTP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!mesh) return set_error(MTP_EINVAL, "mesh is NULL");
+    if (!(cf > 0 && cf < 1)) return set_error(MTP_EINVAL, "causality factor must be in (0, 1)");
+    if (!(T > 0) || !std::isfinite(T)) return set_error(MTP_EINVAL, "T must be positive and finite");
+    auto h = std::make_unique<mtp_tents>();
+    h->t.mesh = &mesh->m;
+    PitchGraph g;
+    int rc = pitch_graph(mesh->m, wavespeed, cf, g);
+    if (rc != MTP_OK) return rc;
+    rc = device_pitch(mesh->m, g, T, h->t, stream);
+    if (rc != MTP_OK) return rc;
+    pitch_finish(mesh->m, T, cf, h->t);
     *out = h.release();
     return MTP_OK;
     MTP_GUARD_END

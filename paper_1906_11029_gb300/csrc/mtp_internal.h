@@ -89,8 +89,17 @@ struct Batch {
 // error reporting
 int set_error(int code, const std::string& msg);
 
-// pitcher (host)
+// pitcher: vertex graph with per-edge bounds b_VW (rows sorted by neighbour id), host
+// rounds, device rounds (mtp_pitch.cu), and the common tail (spacetime DOF count, T, cf)
+struct PitchGraph {
+    std::vector<int64_t> ptr;   // [nv + 1]
+    std::vector<int32_t> dst;   // neighbours W of V: dst[ptr[V] .. ptr[V+1])
+    std::vector<double> bnd;    // b_VW beside each neighbour
+};
+int pitch_graph(const Mesh& mesh, const double* wavespeed, double cf, PitchGraph& g);
 int pitch(const Mesh& mesh, const double* wavespeed, double cf, double T, Tents& out);
+int device_pitch(const Mesh& mesh, const PitchGraph& g, double T, Tents& out, void* stream);
+void pitch_finish(const Mesh& mesh, double T, double cf, Tents& out);
 
 // device side (mtp_cuda.cu)
 int device_mesh_upload(Mesh& m);

@@ -45,6 +45,13 @@ def test_mesh_errors():
     with pytest.raises(mtp.MtpError) as ex:
         m.pitch(0.5, causality_factor=1.5)
     assert ex.value.code == mtp.MTP_EINVAL
+    for T, cf in ((0.5, 1.5), (-1.0, 0.5), (float("inf"), 0.5)):   # checked before any device work
+        with pytest.raises(mtp.MtpError) as ex:
+            m.pitch(T, causality_factor=cf, device=True)
+        assert ex.value.code == mtp.MTP_EINVAL
+    with pytest.raises(mtp.MtpError) as ex:
+        m.pitch(0.5, wavespeed=np.zeros(len(e)), device=True)
+    assert ex.value.code == mtp.MTP_EINVAL
 
 
 def test_mesh_info():
