@@ -120,18 +120,43 @@ class Clocks:
                 "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
 
 
-def cpu_baseline_sample(workload, n_tents, seed=7):
+def cpu_baseline_sample(workload, n_tents, seed=7, procs=1, warmup=0, steps=1):
     """Time the FP64 oracle (test infrastructure, as it stands) on a bounded sample of the
     workload: the first n_tents tents (in layer order, from the flat front t = 0) applied to a
-    seeded random state.
-    Runs in a child process pinned to one BLAS thread; returns the JSON it prints."""
+    seeded random state, `warmup` untimed and `steps` timed repetitions.  With procs > 1 the
+    tents of each layer (independent, Sec. 2) are spread over a pool of that many processes.
+    Runs in a child process with one BLAS thread per process; returns the JSON it prints."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", workload,
-                        "--cpu-tents", str(n_tents), "--seed", str(seed), "--cpu-rounds", "80"],
+                        "--cpu-tents", str(n_tents), "--seed", str(seed), "--cpu-rounds", "80",
+                        "--cpu-procs", str(procs), "--warmup", str(warmup), "--steps", str(steps)],
                        capture_output=True, text=True, env=env, cwd=ROOT)
     if r.returncode != 0:
         return {"error": r.stderr[-400:]}
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+_ORACLE = {}
+
+
+def _oracle_init(workload, barrier):
+    from oracle.mesh import Mesh as OMesh
+    from oracle.mtp import Discretization
+    w = make_workload(workload)
+    _ORACLE["disc"] = Discretization(OMesh(w.verts, w.elems, w.eps, w.mu), w.p)
+    barrier.wait()
+
+
+def _oracle_tent(job):
+    V, dt, tau, Yp = job
+    return _ORACLE["disc"].sat_tent(V, dt, tau, Yp)
 
 
 def cpu_worker(args):
@@ -141,46 +166,72 @@ def cpu_worker(args):
     w = make_workload(args.cpu_worker)
     disc = Discretization(OMesh(w.verts, w.elems, w.eps, w.mu), w.p)
     tents = pitch_tents(w.verts, w.elems, w.eps, w.mu, w.T, w.causality, max_rounds=args.cpu_rounds)
-    rng = np.random.default_rng(args.seed)
-    Y = rng.standard_normal((len(w.elems), disc.nf * disc.nb))
-    tau = np.zeros(len(w.verts))
     n = min(args.cpu_tents, len(tents["vertex"]))
-    dofs = 0.0
-    t0 = time.perf_counter()
-    for t in range(n):                    # (layer, vertex) order: any prefix respects the DAG
-        V = int(tents["vertex"][t])
-        tb, tt = float(tents["t_bot"][t]), float(tents["t_top"][t])
-        patch = disc.mesh.patch[V]
-        slots, Yp = disc.sat_tent(V, tt - tb, tau, Y[patch])
-        Y[slots] = Yp
-        tau[V] = tt
-        dofs += len(patch) * disc.nf * disc.nb * (2 * w.p) * (w.p + 1)
-    dt = time.perf_counter() - t0
-    print(json.dumps({"value": dofs / dt, "seconds": dt, "tents": n, "dofs": dofs}))
+    layers = tents["layer"][:n]
+    pool = None
+    if args.cpu_procs > 1:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(args.cpu_procs)
+        pool = ctx.Pool(args.cpu_procs, initializer=_oracle_init, initargs=(args.cpu_worker, barrier))
+        pool.map(abs, range(args.cpu_procs))          # every worker has built its oracle
+    rates, secs = [], []
+    for rep in range(args.warmup + args.steps):
+        rng = np.random.default_rng(args.seed + rep)
+        Y = rng.standard_normal((len(w.elems), disc.nf * disc.nb))
+        tau = np.zeros(len(w.verts))
+        dofs = 0.0
+        t0 = time.perf_counter()
+        t = 0
+        while t < n:                          # (layer, vertex) order: any prefix respects the DAG
+            e = t
+            while e < n and layers[e] == layers[t]:
+                e += 1
+            jobs = []
+            for i in range(t, e):
+                V = int(tents["vertex"][i])
+                jobs.append((V, float(tents["t_top"][i]) - float(tents["t_bot"][i]), tau, Y[disc.mesh.patch[V]]))
+            res = pool.map(_oracle_tent, jobs) if pool else [disc.sat_tent(*j) for j in jobs]
+            for i, (slots, Yp) in zip(range(t, e), res):
+                V = int(tents["vertex"][i])
+                Y[slots] = Yp
+                tau[V] = float(tents["t_top"][i])
+                dofs += len(disc.mesh.patch[V]) * disc.nf * disc.nb * (2 * w.p) * (w.p + 1)
+            t = e
+        dt = time.perf_counter() - t0
+        if rep >= args.warmup:
+            rates.append(dofs / dt)
+            secs.append(dt)
+    if pool:
+        pool.close()
+        pool.join()
+    print(json.dumps({"value": float(np.mean(rates)), "values": rates, "seconds": float(np.mean(secs)),
+                      "tents": n, "procs": args.cpu_procs}))
 
 
 def run_reference(args):
-    """The FP64 CPU oracle on host cores, bounded sample per step (rank 0 only)."""
+    """The FP64 CPU oracle on all host cores (the tents of a layer spread over a process pool),
+    bounded sample per step (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     w = make_workload(args.workload)
-    vals = []
-    for _ in range(args.warmup):
-        cpu_baseline_sample(args.workload, 2)
-    for s in range(args.steps):
-        vals.append(cpu_baseline_sample(args.workload, args.ref_tents, seed=100 + s))
-    rate = float(np.mean([v["value"] for v in vals]))
-    secs = float(np.mean([v["seconds"] for v in vals]))
+    cores = min(host_cores(), args.cpu_max_procs)
+    n = args.ref_tents * cores
+    r = cpu_baseline_sample(args.workload, n, seed=100, procs=cores, warmup=args.warmup, steps=args.steps)
+    if "error" in r:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + r["error"][-200:]}))
+        return
+    rate, secs = r["value"], r["seconds"]
+    sample = f"first {r['tents']} tents (layer order) per step, seeded random state, FP64 numpy oracle"
     line = {
         "impl": "reference", "metric": "spacetime DOF-updates/s", "value": rate,
         "unit": "DOF-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "elems": int(len(w.elems)), "p": w.p,
-                   "sample": f"first {args.ref_tents} tents (layer order) per step, seeded random state"},
-        "cpu_baseline": {"value": rate, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
-                         "sample": f"first {args.ref_tents} tents (layer order) per step"},
+        "config": {"workload": w.name, "elems": int(len(w.elems)), "p": w.p, "sample": sample},
+        "cpu_baseline": {"value": rate, "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample + f", tents of each layer over {cores} processes"},
         "e2e": {"value": rate, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -453,10 +504,16 @@ def run_mtp(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        r = cpu_baseline_sample(args.workload, args.cpu_tents)
-        cpu = {"value": r.get("value"), "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+        cores = min(host_cores(), args.cpu_max_procs)
+        r = cpu_baseline_sample(args.workload, args.cpu_tents * cores, procs=cores)
+        r1 = cpu_baseline_sample(args.workload, args.cpu_tents)
+        cpu = {"value": r.get("value"), "unit": "DOF-updates/s", "cores": cores, "kind": "oracle",
                "sample": f"first {r.get('tents')} tents (layer order) of the same workload, seeded random "
-                         f"state, FP64 numpy oracle, {r.get('seconds', 0):.1f} s", **({"error": r["error"]} if "error" in r else {})}
+                         f"state, FP64 numpy oracle, tents of each layer over {cores} processes, "
+                         f"{r.get('seconds', 0):.1f} s",
+               "one_core": {"value": r1.get("value"), "sample": f"first {r1.get('tents')} tents, "
+                                                                 f"{r1.get('seconds', 0):.1f} s"},
+               **({"error": (r.get("error") or "") + (r1.get("error") or "")} if "error" in r or "error" in r1 else {})}
 
     if rank == 0:
         line = {
@@ -490,9 +547,11 @@ def main():
     ap.add_argument("--fp64-window", type=float, default=0.02)
     ap.add_argument("--layer-launches", action="store_true", help="one launch per layer instead of the DAG walk")
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
-    ap.add_argument("--cpu-tents", type=int, default=80)
+    ap.add_argument("--cpu-tents", type=int, default=80, help="oracle baseline: tents (per process)")
     ap.add_argument("--cpu-rounds", type=int, default=80)
-    ap.add_argument("--ref-tents", type=int, default=6)
+    ap.add_argument("--ref-tents", type=int, default=20, help="reference arm: tents per host core per step")
+    ap.add_argument("--cpu-procs", type=int, default=1, help="oracle worker: processes over the tents of a layer")
+    ap.add_argument("--cpu-max-procs", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-worker", default=None)
     ap.add_argument("--profile-window", default=None, help="a:b -> apply layers [a, b) once and exit")
