@@ -58,7 +58,7 @@ extern "C" {
 
 /* precision of the state and of the operator arithmetic */
 #define MTP_FP64   0   /* FP64 state and arithmetic */
-#define MTP_FP32   1   /* FP32 state and arithmetic (geometry and G^-1 built in FP64) */
+#define MTP_FP32   1   /* FP32 state and arithmetic (element geometry and causality test in FP64) */
 #define MTP_TF32   2   /* 3D: FP32 state; traces, volume and lift contractions on tensor cores
                           with TF32 operands and FP32 accumulation */
 #define MTP_TF32X3 3   /* 3D: as MTP_TF32 with each operand split into TF32 hi + lo parts and
