@@ -366,6 +366,20 @@ def run_equal_error(args):
     print(json.dumps(res))
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank gets it); `dist` None for one process."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, dofs_per_step, max_ms):
+    """Units of all ranks (each rank evolves its own replica) over the slowest rank's time."""
+    return world * steps * dofs_per_step / (max_ms / 1e3)
+
+
 def run_mtp(args):
     import torch
     import paper_1906_11029_gb300 as mtp
@@ -429,11 +443,8 @@ def run_mtp(args):
     barrier()
     total_ms = start.elapsed_time(end)
     kern_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_max = torch.tensor([total_ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
-    value = world * args.steps * dofs / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
+    value = whole_job_rate(world, args.steps, dofs, total_ms)
 
     # roofline of the tent kernel (the evolve is the tent-kernel graph)
     fl = flops_per_dof_update(w.dim, w.p)

@@ -1,0 +1,66 @@
+"""Host logic of bench.py's multi-process path (one rank per GPU, replicas of the workload):
+the slowest rank's time is what every rank reports, and the value counts the units of all
+ranks.  Run as two gloo ranks on the CPU; the reference arm does no work on rank 1."""
+import importlib.util
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as tmp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    b = _bench()
+    local_ms = [1000.0, 3000.0][rank]
+    m = b.max_over_ranks(local_ms, dist, "cpu")
+    out[rank] = (m, b.whole_job_rate(world, 2, 1e9, m))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_report_the_slowest_time_and_the_whole_job_rate():
+    port = _free_port()
+    out = tmp.Manager().dict()
+    tmp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
+    for r in (0, 1):
+        m, v = out[r]
+        assert m == 3000.0
+        assert v == pytest.approx(2 * 2 * 1e9 / 3.0)
+
+
+def test_single_process_needs_no_group():
+    b = _bench()
+    assert b.max_over_ranks(12.5, None, "cpu") == 12.5
+    assert b.whole_job_rate(1, 4, 2e9, 1000.0) == pytest.approx(8e9)
+
+
+def test_reference_arm_does_nothing_on_other_ranks(capsys, monkeypatch):
+    b = _bench()
+    monkeypatch.setenv("RANK", "1")
+    calls = []
+    monkeypatch.setattr(b, "cpu_baseline_sample", lambda *a, **k: calls.append(a) or {})
+
+    class A:
+        workload, warmup, steps, gpus, ref_tents, cpu_max_procs = "graded", 3, 2, 2, 20, 16
+    assert b.run_reference(A()) is None
+    assert calls == [] and capsys.readouterr().out == ""
