@@ -9,7 +9,8 @@ a wrong sign or index, a transposed operand) would break:
   flux; exact Riemann transmission at a material jump; PEC kills tangential E
 * whole-tent polynomial exactness (Sec. 3 + Sec. 4): a polynomial plane wave is
   reproduced to round-off by one tent step (interior tent and PEC tent, 2D and 3D)
-* SAT vs brute-force RK4 on the tent ODE d/dt[M U] = A U (Sec. 3, eq. equ_ode)
+* SAT vs brute-force RK4 on the tent ODE d/dt[M U] = A U (Sec. 3, eq. equ_ode); with a
+  constant M (M' = 0) each sub-interval is the degree-q Taylor polynomial of exp(A M^-1 / m)
 * pitcher invariants (Sec. 2): causality slope, independence of a layer, final front
 * energy non-increase and O(h^{p+1}) convergence (Sec. 5.1)
 * the spacetime DOF counter against Table 1
@@ -238,6 +239,27 @@ def test_tent_exactness_detects_planted_sign_error(monkeypatch):
 
 
 # ----------------------------------------------------------------------------- SAT vs RK4
+@pytest.mark.parametrize("q,msub", [(1, 1), (3, 2), (5, 8)])
+def test_sat_with_constant_mass_is_truncated_exponential(q, msub):
+    """Sec. 4 recursion with M' = 0: Y_{i,n} = (A M^-1)^n Y_{i,0}, so one sub-interval maps Y to
+    sum_{n<=q} (A M^-1 / m)^n / n! Y and the tent applies that m times.  The operators are
+    random (two patch elements, coupled blocks); the expectation is plain matrix algebra."""
+    w = S.te_square(2, 1, 0.1)
+    disc = Discretization(Mesh(w.verts, w.elems, w.eps, w.mu), w.p)
+    rng = np.random.default_rng(5)
+    N, ns = disc.nf * disc.nb, 2
+    M0 = [np.eye(N) * 2.0 + 0.1 * rng.standard_normal((N, N)) for _ in range(ns)]
+    Mp = [np.zeros((N, N)) for _ in range(ns)]
+    A = {(a, b): 0.3 * rng.standard_normal((N, N)) for a in range(ns) for b in range(ns)}
+    disc.tent_operators = lambda V, dt, tau: ([0, 1], M0, Mp, A)
+    Y0 = rng.standard_normal((ns, N))
+    _, Y = disc.sat_tent(0, 0.1, None, Y0, q=q, msub=msub)
+    K = np.block([[A[(a, b)] @ np.linalg.inv(M0[b]) for b in range(ns)] for a in range(ns)]) / msub
+    step = sum(np.linalg.matrix_power(K, n) / math.factorial(n) for n in range(q + 1))
+    expect = np.linalg.matrix_power(step, msub) @ Y0.reshape(-1)
+    assert np.allclose(Y.reshape(-1), expect, rtol=1e-12, atol=1e-12)
+
+
 def test_sat_converges_to_rk4_solution_of_tent_ode():
     v, e = S.cube_mesh(2)
     rng = np.random.default_rng(4)
