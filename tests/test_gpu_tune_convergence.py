@@ -1,6 +1,6 @@
 """Launch configurations and the autotuner on the GPU, and the paper's convergence claim
 (Sec. 5.1, Fig. 3 left) reproduced with the CUDA path: O(h^{p+1}) for p = 1..4 with
-(p+1)-stage SAT and m = 2p on the 2D cavity."""
+(p+1)-stage SAT and m = 2p on the 2D cavity, and for p = 1..3 on the 3D (1,1,1) cavity mode."""
 import math
 import os
 
@@ -80,4 +80,26 @@ def test_cavity_convergence_rate_gpu(p):
     errs = [_lattice_error(p, n) for n in ns]
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     print(f"p={p} errors {['%.2e' % e for e in errs]} rates {['%.2f' % r for r in rates]}")
+    assert rates[-1] > p + 0.7, (errs, rates)
+
+
+def _lattice_error_3d(p, n):
+    w = S.cube_mode(n, p, 0.25, perturb=0.0)
+    m = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=p)
+    t = m.pitch(w.T)
+    st = m.state_from_lattice(torch.tensor(_vals(w), device=DEV))
+    t.evolve(st)
+    got = m.state_to_lattice(st).cpu().numpy()[0]
+    pts = S.lattice_points(w.verts, w.elems, p)
+    E, H = w.exact(pts, w.T)
+    ref = np.concatenate([E, H], -1)
+    return float(np.linalg.norm(got - ref) / math.sqrt(ref.size))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_cube_cavity_convergence_rate_gpu(p):
+    ns = (4, 8, 16)
+    errs = [_lattice_error_3d(p, n) for n in ns]
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    print(f"3D p={p} errors {['%.2e' % e for e in errs]} rates {['%.2f' % r for r in rates]}")
     assert rates[-1] > p + 0.7, (errs, rates)
