@@ -28,6 +28,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace mtp {
@@ -70,6 +71,16 @@ struct KArgs {
 };
 
 __host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
+// dim P_k on a simplex of dimension `dim` (0 for k < 0), and the degree of the r-th basis
+// function when the basis is ordered by total degree (as the reference tables are)
+__host__ __device__ constexpr int dim_pk(int dim, int k) {
+    return k < 0 ? 0 : dim == 1 ? k + 1 : dim == 2 ? (k + 1) * (k + 2) / 2 : (k + 1) * (k + 2) * (k + 3) / 6;
+}
+__host__ __device__ constexpr int degree_of(int dim, int r) {
+    int k = 0;
+    while (r >= dim_pk(dim, k)) ++k;
+    return k;
+}
 
 template <int DIM, int P>
 struct Shape {
@@ -84,6 +95,15 @@ struct Shape {
     static constexpr int AP = 2;                       // basis functions per thread
     static constexpr int NAG = (NB + AP - 1) / AP;     // basis groups per element
     static constexpr int NCG = (NFB + AP - 1) / AP;    // facet-mode groups per facet
+    // Degree structure of the tables (basis ordered by degree): S[a][b] = 0 for deg b > deg a
+    // and Tr[c][b] = 0 for deg b < deg c.  A thread's first row a = g < NAG has degree
+    // < P when NAG <= dim P_{P-1}, so the volume term needs it only for b < NBLO; its second
+    // facet row c = g + NCG has degree >= TDEG, so the traces need it only for
+    // b >= dim P_{TDEG-1}.
+    static constexpr int NBLO = dim_pk(DIM, P - 1);
+    static constexpr bool VSPLIT = NAG <= NBLO;
+    static constexpr int TDEG = degree_of(DIM - 1, NCG);
+    static constexpr int TLO = dim_pk(DIM, TDEG - 1);
 };
 
 // CTAs per SM the register budget is shaped for (two 256-thread CTAs fit the FP32 3D
@@ -421,13 +441,14 @@ __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real
             for (int ci = 0; ci < AP; ++ci)
 #pragma unroll
                 for (int s = 0; s < NF; ++s) acc[fi][ci][s] = 0;
-#pragma unroll 1
-        for (int b = 0; b < NBP; b += W) {
+        // column block [b, b + W) for the first row only (NR = 1) or both rows (NR = 2)
+        auto block = [&](int b, auto nr) {
+            constexpr int NR = decltype(nr)::value;
             Real tv[DIM][AP][W];
 #pragma unroll
             for (int fi = 0; fi < DIM; ++fi)
 #pragma unroll
-                for (int ci = 0; ci < AP; ++ci)
+                for (int ci = 0; ci < NR; ++ci)
                     Vec<Real>::get(__ldg((const VT*)(T[fi] + b * AP * NCG + ci * NCG * W)), tv[fi][ci]);
 #pragma unroll
             for (int s = 0; s < NF; ++s) {
@@ -438,9 +459,14 @@ __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real
 #pragma unroll
                     for (int fi = 0; fi < DIM; ++fi)
 #pragma unroll
-                        for (int ci = 0; ci < AP; ++ci) acc[fi][ci][s] += tv[fi][ci][v] * u[v];
+                        for (int ci = 0; ci < NR; ++ci) acc[fi][ci][s] += tv[fi][ci][v] * u[v];
             }
-        }
+        };
+        constexpr int BT = Sh::TLO / W * W;   // second rows vanish on the blocks below
+#pragma unroll 1
+        for (int b = 0; b < BT; b += W) block(b, std::integral_constant<int, 1>{});
+#pragma unroll 1
+        for (int b = BT; b < NBP; b += W) block(b, std::integral_constant<int, 2>{});
         const Real sc = c.sTrs[k];
 #pragma unroll
         for (int fi = 0; fi < DIM; ++fi) {
@@ -529,14 +555,15 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
 #pragma unroll
                         for (int s = 0; s < NF; ++s) Pm[e][ai][l][s] = 0;
             const Real* Sg = S + (size_t)j * DIM * SMAT + ag * W;
-#pragma unroll 1
-            for (int b = 0; b < NBP; b += W) {
+            // column block [b, b + W) for both rows (A0 = 0) or the second row only (A0 = 1)
+            auto block = [&](int b, auto a0) {
+                constexpr int A0 = decltype(a0)::value;
                 Real sv[AP][DIM][W];
                 const Real* Sb = Sg + b * AP * NAG;
 #pragma unroll
                 for (int l = 0; l < DIM; ++l)
 #pragma unroll
-                    for (int ai = 0; ai < AP; ++ai)
+                    for (int ai = A0; ai < AP; ++ai)
                         Vec<Real>::get(__ldg((const VT*)(Sb + l * SMAT + ai * NAG * W)), sv[ai][l]);
 #pragma unroll
                 for (int e = 0; e < EP; ++e) {
@@ -548,12 +575,18 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
 #pragma unroll
                         for (int v = 0; v < W; ++v)
 #pragma unroll
-                            for (int ai = 0; ai < AP; ++ai)
+                            for (int ai = A0; ai < AP; ++ai)
 #pragma unroll
                                 for (int l = 0; l < DIM; ++l) Pm[e][ai][l][s] += sv[ai][l][v] * u[v];
                     }
                 }
-            }
+            };
+            // first rows (degree < P) vanish from block BV on
+            constexpr int BV = Sh::VSPLIT ? (Sh::NBLO + W - 1) / W * W : NBP;
+#pragma unroll 1
+            for (int b = 0; b < BV; b += W) block(b, std::integral_constant<int, 0>{});
+#pragma unroll 1
+            for (int b = BV; b < NBP; b += W) block(b, std::integral_constant<int, 1>{});
 #pragma unroll
             for (int e = 0; e < EP; ++e) {
                 const Real* ac = c.sAc + kk[e] * DIM * 3;

@@ -10,6 +10,7 @@
 // arithmetic); every reference integral below is then evaluated by the monomial
 // formula  int_{unit d-simplex} x^a y^b z^c = a! b! c! / (a+b+c+d)!,  so the tables
 // carry no quadrature error.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
@@ -138,19 +139,29 @@ std::vector<Poly> homog_jacobi(int nmax, int alpha, const Poly& t, const Poly& s
 }
 
 // Orthonormal Dubiner basis of P_p on the unit simplex of dimension d (d = 1, 2, 3),
-// ordered by (i, j, k) loops; variables x, y, z.
-std::vector<Poly> dubiner(int d, int p) {
+// variables x, y, z, ordered by total degree (ties in (i, j, k) loop order); `deg`
+// receives each function's degree.  psi_{ijk} has degree i + j + k and is orthogonal to
+// every polynomial of lower degree, which makes the reference tables block-triangular
+// in the degree (see build_ref_tables).
+std::vector<Poly> dubiner(int d, int p, std::vector<int>* deg = nullptr) {
     Poly X = Poly::var(0), Y = Poly::var(1), Z = Poly::var(2), one = Poly::cst(1);
     std::vector<Poly> out;
+    std::vector<int> dg;
     if (d == 1) {
         auto H = homog_jacobi(p, 0, add(scale(X, 2), one, -1), one);
-        for (int i = 0; i <= p; ++i) out.push_back(H[i]);
+        for (int i = 0; i <= p; ++i) {
+            out.push_back(H[i]);
+            dg.push_back(i);
+        }
     } else if (d == 2) {
         Poly s1 = add(one, Y, -1), t1 = add(add(scale(X, 2), Y), one, -1);
         auto Hi = homog_jacobi(p, 0, t1, s1);
         for (int i = 0; i <= p; ++i) {
             auto Jj = homog_jacobi(p - i, 2 * i + 1, add(scale(Y, 2), one, -1), one);
-            for (int j = 0; i + j <= p; ++j) out.push_back(mul(Hi[i], Jj[j]));
+            for (int j = 0; i + j <= p; ++j) {
+                out.push_back(mul(Hi[i], Jj[j]));
+                dg.push_back(i + j);
+            }
         }
     } else {
         Poly s1 = add(add(one, Y, -1), Z, -1), t1 = add(add(add(scale(X, 2), Y), Z), one, -1);
@@ -161,12 +172,25 @@ std::vector<Poly> dubiner(int d, int p) {
             for (int j = 0; i + j <= p; ++j) {
                 auto Jk = homog_jacobi(p - i - j, 2 * i + 2 * j + 2, add(scale(Z, 2), one, -1), one);
                 Poly ij = mul(Hi[i], Hj[j]);
-                for (int k = 0; i + j + k <= p; ++k) out.push_back(mul(ij, Jk[k]));
+                for (int k = 0; i + j + k <= p; ++k) {
+                    out.push_back(mul(ij, Jk[k]));
+                    dg.push_back(i + j + k);
+                }
             }
         }
     }
     for (auto& b : out) b = scale(b, 1.0L / std::sqrt(integrate(mul(b, b), d)));
-    return out;
+    std::vector<int> order(out.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dg[a] < dg[b]; });
+    std::vector<Poly> sorted;
+    std::vector<int> sdeg;
+    for (int i : order) {
+        sorted.push_back(out[i]);
+        sdeg.push_back(dg[i]);
+    }
+    if (deg) *deg = sdeg;
+    return sorted;
 }
 
 Poly lambda_poly(int d, int j) {
@@ -220,8 +244,9 @@ void invert(std::vector<ld>& A, int n) {
 RefTables build_ref_tables(int d, int p) {
     RefTables t;
     t.dim = d; t.p = p;
-    auto psi = dubiner(d, p);
-    auto chi = dubiner(d - 1, p);
+    std::vector<int> dpsi_deg, dchi_deg;
+    auto psi = dubiner(d, p, &dpsi_deg);
+    auto chi = dubiner(d - 1, p, &dchi_deg);
     const int nb = t.nb = (int)psi.size();
     const int nfb = t.nfb = (int)chi.size();
     std::vector<Poly> lam(d + 1), dpsi[3];
@@ -264,6 +289,24 @@ RefTables build_ref_tables(int d, int p) {
             }
         }
     }
+    // Exact zeros left as rounding residue by the polynomial arithmetic: chi_c and psi_b are
+    // orthogonal to every polynomial of lower degree, so S[j][l][a][b] = 0 for
+    // deg b > deg a (lambda_j d_l psi_a has degree <= deg a), Tr[f][c][b] = 0 for
+    // deg b < deg c, and L[j][f][a][c] = 0 for deg c > deg a + 1.  The tent kernels skip
+    // these blocks; every table states them exactly.
+    for (int j = 0; j <= d; ++j)
+        for (int l = 0; l < d; ++l)
+            for (int a = 0; a < nb; ++a)
+                for (int b = 0; b < nb; ++b)
+                    if (dpsi_deg[b] > dpsi_deg[a]) t.S[(((size_t)j * d + l) * nb + a) * nb + b] = 0.0;
+    for (int f = 0; f <= d; ++f)
+        for (int c = 0; c < nfb; ++c)
+            for (int b = 0; b < nb; ++b)
+                if (dpsi_deg[b] < dchi_deg[c]) t.Tr[((size_t)f * nfb + c) * nb + b] = 0.0;
+    for (size_t jf = 0; jf < (size_t)(d + 1) * (d + 1); ++jf)
+        for (int a = 0; a < nb; ++a)
+            for (int c = 0; c < nfb; ++c)
+                if (dchi_deg[c] > dpsi_deg[a] + 1) t.L[(jf * nb + a) * nfb + c] = 0.0;
     // lattice Vandermonde (point order: i_d outermost, i_1 innermost)
     std::vector<ld> V((size_t)nb * nb);
     int k = 0;
