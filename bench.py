@@ -36,8 +36,8 @@ N_SMS = 152
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per tent of the FP32 p=4 tent
 # kernels on the graded 32^3 workload, from the last ncu capture of the current kernel
 # version; an entry is removed once its kernel has changed since the counters were taken.
-TRAFFIC_BYTES_PER_TENT = {}                           # tent_layer_kernel, per tent
-TRAFFIC_PERSISTENT_BYTES = {}                         # tent_persistent_kernel, per tent (full evolve)
+TRAFFIC_BYTES_PER_TENT = {"fp32": 27529.6}              # tent_layer_kernel, per tent
+TRAFFIC_PERSISTENT_BYTES = {"fp32": 24458.8}            # tent_persistent_kernel, per tent (full evolve)
 
 
 def load_peaks():
