@@ -293,20 +293,32 @@ RefTables build_ref_tables(int d, int p) {
     // orthogonal to every polynomial of lower degree, so S[j][l][a][b] = 0 for
     // deg b > deg a (lambda_j d_l psi_a has degree <= deg a), Tr[f][c][b] = 0 for
     // deg b < deg c, and L[j][f][a][c] = 0 for deg c > deg a + 1.  The tent kernels skip
-    // these blocks; every table states them exactly.
+    // these blocks; every table states them exactly.  Each entry set to zero must already be
+    // rounding residue (checked: a wrong basis order must not silently change the operator).
+    auto zero = [](double& v, double scale) {
+        if (!(std::fabs(v) <= 1e-10 * scale)) throw std::runtime_error("reference tables: degree structure violated");
+        v = 0.0;
+    };
+    // the tent kernels' loop bounds assume both bases in ascending degree
+    if (!std::is_sorted(dpsi_deg.begin(), dpsi_deg.end()) || !std::is_sorted(dchi_deg.begin(), dchi_deg.end()))
+        throw std::runtime_error("reference tables: basis not ordered by degree");
+    double smax = 0, tmax = 0, lmax = 0;
+    for (double v : t.S) smax = std::fmax(smax, std::fabs(v));
+    for (double v : t.Tr) tmax = std::fmax(tmax, std::fabs(v));
+    for (double v : t.L) lmax = std::fmax(lmax, std::fabs(v));
     for (int j = 0; j <= d; ++j)
         for (int l = 0; l < d; ++l)
             for (int a = 0; a < nb; ++a)
                 for (int b = 0; b < nb; ++b)
-                    if (dpsi_deg[b] > dpsi_deg[a]) t.S[(((size_t)j * d + l) * nb + a) * nb + b] = 0.0;
+                    if (dpsi_deg[b] > dpsi_deg[a]) zero(t.S[(((size_t)j * d + l) * nb + a) * nb + b], smax);
     for (int f = 0; f <= d; ++f)
         for (int c = 0; c < nfb; ++c)
             for (int b = 0; b < nb; ++b)
-                if (dpsi_deg[b] < dchi_deg[c]) t.Tr[((size_t)f * nfb + c) * nb + b] = 0.0;
+                if (dpsi_deg[b] < dchi_deg[c]) zero(t.Tr[((size_t)f * nfb + c) * nb + b], tmax);
     for (size_t jf = 0; jf < (size_t)(d + 1) * (d + 1); ++jf)
         for (int a = 0; a < nb; ++a)
             for (int c = 0; c < nfb; ++c)
-                if (dchi_deg[c] > dpsi_deg[a] + 1) t.L[(jf * nb + a) * nfb + c] = 0.0;
+                if (dchi_deg[c] > dpsi_deg[a] + 1) zero(t.L[(jf * nb + a) * nfb + c], lmax);
     // lattice Vandermonde (point order: i_d outermost, i_1 innermost)
     std::vector<ld> V((size_t)nb * nb);
     int k = 0;

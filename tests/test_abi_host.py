@@ -110,3 +110,16 @@ def test_tensor_core_precision_is_3d_only():
     with pytest.raises(mtp.MtpError) as ex:
         mtp.Mesh(2, v, e, np.ones(len(e)), np.ones(len(e)), p=2, precision=mtp.MTP_TF32)
     assert ex.value.code == mtp.MTP_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_reference_tables_build_for_every_degree(dim):
+    """Mesh creation builds the reference tables; it fails if either basis is not in
+    ascending degree order or if an entry that the degree structure makes zero is more than
+    rounding residue (the tent kernels skip those blocks)."""
+    v, e = S.square_mesh(2) if dim == 2 else S.cube_mesh(2)
+    one = np.ones(len(e))
+    for p in range(1, 6):
+        m = mtp.Mesh(dim, v, e, one, one, p=p)
+        nb = (p + 1) * (p + 2) // 2 if dim == 2 else (p + 1) * (p + 2) * (p + 3) // 6
+        assert m.info["n_basis"] == nb
