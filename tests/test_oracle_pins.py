@@ -9,6 +9,8 @@ a wrong sign or index, a transposed operand) would break:
   flux; exact Riemann transmission at a material jump; PEC kills tangential E
 * whole-tent polynomial exactness (Sec. 3 + Sec. 4): a polynomial plane wave is
   reproduced to round-off by one tent step (interior tent and PEC tent, 2D and 3D)
+* operator A on a continuous polynomial field at an interior tent equals the moments of
+  -div(delta f(u)) (consistent flux, delta = 0 on the facets away from V)
 * SAT vs brute-force RK4 on the tent ODE d/dt[M U] = A U (Sec. 3, eq. equ_ode); with a
   constant M (M' = 0) each sub-interval is the degree-q Taylor polynomial of exp(A M^-1 / m)
 * pitcher invariants (Sec. 2): causality slope, independence of a layer, final front
@@ -239,6 +241,80 @@ def test_tent_exactness_detects_planted_sign_error(monkeypatch):
 
 
 # ----------------------------------------------------------------------------- SAT vs RK4
+def _poly_field(d, p, rng):
+    """Six random polynomial components of degree <= p in x (z-invariant in 2D): exponents,
+    coefficients, and an evaluator of values and gradients."""
+    exps = [g for g in np.ndindex(*(p + 1,) * 3) if sum(g) <= p and (d == 3 or g[2] == 0)]
+    coef = rng.standard_normal((6, len(exps)))
+
+    def ev(X):                                   # X [Q, d] -> u [Q, 6], grad [Q, 6, 3]
+        X3 = np.zeros((len(X), 3))
+        X3[:, :d] = X
+        mon = np.stack([np.prod(X3 ** np.array(g), 1) for g in exps], 1)
+        grad = np.zeros((len(X), len(exps), 3))
+        for t, g in enumerate(exps):
+            for k in range(3):
+                if g[k]:
+                    h = list(g)
+                    h[k] -= 1
+                    grad[:, t, k] = g[k] * np.prod(X3 ** np.array(h), 1)
+        return mon @ coef.T, np.einsum("qtk,st->qsk", grad, coef)
+    return ev
+
+
+def _curl(gr):                                   # gr [Q, 3 components, 3 derivatives]
+    return np.stack([gr[:, 2, 1] - gr[:, 1, 2], gr[:, 0, 2] - gr[:, 2, 0], gr[:, 1, 0] - gr[:, 0, 1]], 1)
+
+
+@pytest.mark.parametrize("d,p", [(2, 1), (2, 3), (3, 1), (3, 2)])
+def test_operator_a_on_a_continuous_polynomial_is_minus_div_delta_f(d, p):
+    """Sec. 3 weak form: for u continuous and polynomial of degree <= p on the patch of an
+    interior vertex V, every facet flux is consistent (F*(u, u) = f(u) n) and delta = dt
+    lambda_V vanishes on the facets away from V, so integrating by parts element by element
+    gives (A U, v) = -sum_T int_T div(delta f(u)) . v with
+    -div(delta f(u)) = [grad(delta) x H + delta curl H ; -grad(delta) x E - delta curl E]."""
+    rng = np.random.default_rng(17 + 10 * d + p)
+    if d == 2:
+        v, e = S.square_mesh(3)
+        V = 5                                    # interior vertex (1/3, 1/3)
+    else:
+        v, e = S.cube_mesh(2)
+        V = 13                                   # centre of the cube
+    one = np.ones(len(e))
+    disc = Discretization(Mesh(v, e, 2.0 * one, 0.5 * one), p)
+    m = disc.mesh
+    dt = 0.3
+    tau = rng.uniform(0.0, 0.05, m.nv)
+    slots, _, _, A = disc.tent_operators(V, dt, tau)
+    ev = _poly_field(d, p, rng)
+    fs = disc.fs
+    # Bernstein coefficients of u on each patch element (interpolation at the lattice)
+    from mtp_synth import lattice_multi_indices
+    mi = lattice_multi_indices(d, p)
+    U = []
+    for e_ in slots:
+        lam = m.barycentric_of_sorted_lattice(e_, mi, p)
+        X = lam @ m.verts[m.elems[e_]]
+        U.append(np.linalg.solve(bernstein_eval(lam, p), ev(X)[0][:, fs]).T.reshape(-1))
+    got = np.zeros((len(slots), disc.nf * disc.nb))
+    for (a, b), blk in A.items():
+        got[a] += blk @ U[b]
+    lamq, wq = duffy_rule(d, p + 2)
+    Bq = bernstein_eval(lamq, p)
+    for k, e_ in enumerate(slots):
+        j = m.local_index(e_, V)
+        X = lamq @ m.verts[m.elems[e_]]
+        u, gr = ev(X)
+        gd = np.zeros(3)
+        gd[:d] = dt * m.grad_lam[e_][j]
+        delta = dt * lamq[:, j]
+        E, H = u[:, :3], u[:, 3:]
+        w = np.concatenate([np.cross(gd, H) + delta[:, None] * _curl(gr[:, 3:]),
+                            -np.cross(gd, E) - delta[:, None] * _curl(gr[:, :3])], 1)[:, fs]
+        expect = np.einsum("qr,q,qa->ra", w, wq, Bq) * m.vol[e_]
+        assert np.allclose(got[k].reshape(disc.nf, disc.nb), expect, rtol=1e-11, atol=1e-11 * np.abs(expect).max())
+
+
 @pytest.mark.parametrize("q,msub", [(1, 1), (3, 2), (5, 8)])
 def test_sat_with_constant_mass_is_truncated_exponential(q, msub):
     """Sec. 4 recursion with M' = 0: Y_{i,n} = (A M^-1)^n Y_{i,0}, so one sub-interval maps Y to
