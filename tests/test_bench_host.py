@@ -1,6 +1,7 @@
-"""Host logic of bench.py's multi-process path (one rank per GPU, replicas of the workload):
+"""Host logic of bench.py.  Multi-process path (one rank per GPU, replicas of the workload):
 the slowest rank's time is what every rank reports, and the value counts the units of all
-ranks.  Run as two gloo ranks on the CPU; the reference arm does no work on rank 1."""
+ranks; run as two gloo ranks on the CPU; the reference arm does no work on rank 1.  And the
+roofline's algorithmic work counter."""
 import importlib.util
 import os
 import socket
@@ -64,3 +65,11 @@ def test_reference_arm_does_nothing_on_other_ranks(capsys, monkeypatch):
         workload, warmup, steps, gpus, ref_tents, cpu_max_procs = "graded", 3, 2, 2, 20, 16
     assert b.run_reference(A()) is None
     assert calls == [] and capsys.readouterr().out == ""
+
+
+@pytest.mark.parametrize("dim,p,flop", [(2, 2, 60), (3, 2, 156), (3, 3, 264), (3, 4, 414)])
+def test_algorithmic_flops_per_dof_update(dim, p, flop):
+    """The roofline's work counter: per element and operator application, volume d n_f N_p^2,
+    facets d n_f 2 N_fp N_p and mass solve + M' 2 n_f^2 N_p multiply-adds, 2 flop each,
+    divided by the n_f N_p DOFs updated."""
+    assert _bench().flops_per_dof_update(dim, p) == pytest.approx(flop)
