@@ -4,7 +4,7 @@ Sec. 2 starts from a conforming spatial mesh of elements T and vertices V; each
 tent's spatial footprint is the vertex patch omega_V (all elements containing V).
 This module holds the affine geometry of each element (barycentric gradients,
 measure), the facet table (each facet shared by two elements, or on the domain
-boundary, which is PEC everywhere in this build), and vertex adjacency.
+boundary, which is PEC everywhere in this implementation), and vertex adjacency.
 Element vertex order is kept exactly as given; orientation does not matter
 because only |det| and outward normals are used.
 """

@@ -243,7 +243,7 @@ static int build_mesh(int dim, int64_t nv, const double* X, int64_t ne, const in
     const int cap = dim == 2 ? kMaxPatch2D : kMaxPatch3D;
     if (m.max_patch > cap)
         return set_error(MTP_EUNSUPPORTED, "largest vertex patch has " + std::to_string(m.max_patch) +
-                                               " elements; this build supports up to " + std::to_string(cap));
+                                               " elements; the library is compiled for patches of up to " + std::to_string(cap));
     m.ref = ref_tables(dim, o.p);
     return MTP_OK;
 }

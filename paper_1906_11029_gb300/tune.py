@@ -48,7 +48,7 @@ def _save(path, data):
 
 
 def candidates(dim, p, accuracy):
-    """Precision variants that meet the accuracy class on this build."""
+    """Precision variants that the library compiles and that meet the accuracy class."""
     if accuracy == "fp32":
         return [MTP_FP32] + ([MTP_TF32X3] if dim == 3 and p <= 4 else [])
     if accuracy == "tf32":
