@@ -18,8 +18,10 @@ paper defines (arXiv:1906.11029):
 * ``mtp``      per-tent assembly of M(t), M', A on the vertex patch (Sec. 3)
   and the q-stage SAT recursion over m sub-intervals (Sec. 4), the layer-by-
   layer evolution, projection, lattice evaluation, L2 error and energy.
-* ``brute``    brute-force cross-checks: classical RK4 on a tent's ODE and a
-  global (non-tent) DG + RK4 solver.
+* ``brute``    brute-force cross-checks: a global (non-tent) upwind DG + classical
+  RK4 solver built by quadrature, and the Y-substituted classical RK4 tent stepper
+  that Sec. 3 and Sec. 5.1 contrast with SAT.
+* ``adjoint``  the discrete adjoint of the tent evolution (dense transposes).
 
 Every function cites the paper passage (section / equation) it follows.
 Readings of the paper where it is silent or garbled are listed in the

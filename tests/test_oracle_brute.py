@@ -1,0 +1,113 @@
+"""The oracle against a global (non-tent) DG + classical RK4 solver, and the paper's
+negative control, the Y-substituted classical RK4 tent stepper (CPU only).
+
+* The global solver (``oracle.brute.GlobalDG``, quadrature-built, no tent map, no SAT) is
+  pinned on its own against the exact TE cavity mode: O(h^{p+1}).
+* MTP-SAT and the global solver are different discretisations of the same PDE, so on the same
+  mesh their distance shrinks like O(h^{p+1}) (not to round-off).  A planted sign error in
+  the tent scheme's M' term (Sec. 4, eq. coeff_rec) leaves an O(1) distance.
+* Sec. 3 (after eq. equ_ode) and Sec. 5.1 (Fig. 3 right): integrating d/dt Y = A M^-1 Y on
+  the tents with classical RK4 loses the optimal order.  Measured here as the distance
+  between the RK4 and the SAT results on the same tents (the RK4 time-stepping error): it
+  falls at an order of about 1 to 2 whatever p is, while SAT's error falls at p + 1; at
+  p = 4 it is already as large as SAT's whole discretisation error on an 8 x 8 mesh.
+"""
+import numpy as np
+import pytest
+
+import mtp_synth as S
+from oracle.brute import GlobalDG, evolve_substituted_rk4, rk4_global
+from oracle.mesh import Mesh
+from oracle.mtp import Discretization
+from oracle.pitch import pitch_tents
+
+
+def _zero(X, t):
+    z = np.zeros(X.shape[:-1] + (3,))
+    return z, z
+
+
+def _mtp(w, tents=None):
+    disc = Discretization(Mesh(w.verts, w.elems, w.eps, w.mu), w.p)
+    tents = tents or pitch_tents(w.verts, w.elems, w.eps, w.mu, w.T, w.causality)
+    Y, _ = disc.evolve(disc.project_initial(w.init), tents)
+    return disc, disc.fields_at_flat_front(Y)
+
+
+def _dg(w, steps_per_unit=800):
+    dg = GlobalDG(Mesh(w.verts, w.elems, w.eps, w.mu), w.p)
+    n_steps = max(1, int(round(steps_per_unit * w.T * len(w.verts) ** (1.0 / w.dim))))
+    return dg, rk4_global(dg, dg.project(w.init), w.T, n_steps)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_global_dg_rk4_converges_to_te_mode(p):
+    errs = []
+    for n in (2, 4, 8):
+        w = S.te_square(n, p, 0.25)
+        dg, U = _dg(w)
+        errs.append(dg.l2_error(U, w.exact, w.T))
+    rates = np.log2(np.array(errs[:-1]) / errs[1:])
+    assert rates.min() > p + 0.7, (errs, rates)
+
+
+def test_global_dg_energy_and_3d_mode():
+    """Upwind DG dissipates (energy non-increasing) and converges on the 3D (1,1,1) mode too."""
+    errs = []
+    for n in (1, 2):
+        w = S.cube_mode(n, 2, 0.1, perturb=0.0)
+        dg, U = _dg(w, 400)
+        errs.append(dg.l2_error(U, w.exact, w.T))
+        U0 = dg.project(w.init)
+        assert dg.energy(U) <= dg.energy(U0) * (1 + 1e-12)
+    assert errs[1] < errs[0] / 4, errs
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_mtp_and_global_dg_agree_to_discretisation_order(p):
+    dists = []
+    for n in (2, 4, 8):
+        w = S.te_square(n, p, 0.25)
+        disc, Um = _mtp(w)
+        dg, Ud = _dg(w)
+        dists.append(dg.l2_error(Um - Ud, _zero, 0.0))
+    rates = np.log2(np.array(dists[:-1]) / dists[1:])
+    assert rates.min() > p + 0.6, (dists, rates)
+
+
+def test_mtp_vs_dg_detects_planted_mprime_sign(monkeypatch):
+    orig = Discretization.tent_operators
+
+    def planted(self, V, dt, tau):
+        slots, M0, Mp, A = orig(self, V, dt, tau)
+        return slots, M0, [-x for x in Mp], A
+
+    monkeypatch.setattr(Discretization, "tent_operators", planted)
+    dists = []
+    for n in (2, 4):
+        w = S.te_square(n, 2, 0.25)
+        disc, Um = _mtp(w)
+        dg, Ud = _dg(w)
+        dists.append(dg.l2_error(Um - Ud, _zero, 0.0))
+    assert dists[1] > dists[0] / 2.5 and dists[1] > 1e-2, dists
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_substituted_rk4_loses_order_while_sat_keeps_it(p):
+    sat_err, rk_dist = [], []
+    for n in (2, 4, 8):
+        w = S.te_square(n, p, 0.25)
+        disc = Discretization(Mesh(w.verts, w.elems, w.eps, w.mu), p)
+        tents = pitch_tents(w.verts, w.elems, w.eps, w.mu, w.T, 0.5)
+        Y0 = disc.project_initial(w.init)
+        Ys, _ = disc.evolve(Y0, tents)
+        Yr = evolve_substituted_rk4(disc, Y0, tents, 2 * p)
+        Us, Ur = disc.fields_at_flat_front(Ys), disc.fields_at_flat_front(Yr)
+        sat_err.append(disc.l2_error(Us, w.exact, w.T))
+        rk_dist.append(disc.l2_error(Ur - Us, _zero, 0.0))
+    sat_rate = np.log2(sat_err[1] / sat_err[2])
+    rk_rate = np.log2(rk_dist[1] / rk_dist[2])
+    assert sat_rate > p + 0.8, sat_err
+    assert rk_rate < 2.5, rk_dist
+    if p == 4:
+        assert rk_dist[2] > 0.5 * sat_err[2], (rk_dist, sat_err)

@@ -27,7 +27,7 @@ import pytest
 import mtp_synth as S
 from oracle import maxwell as mx
 from oracle.mesh import Mesh
-from oracle.mtp import Discretization, front_before_layer
+from oracle.mtp import Discretization, front_before_layer, spacetime_dofs
 from oracle.pitch import pitch_tents
 from oracle.simplex import bernstein_eval, duffy_rule, monomial_integral, multi_indices
 
@@ -464,16 +464,29 @@ def test_convergence_rate_te_mode(p):
 
 # ----------------------------------------------------------------------------- metric
 def test_spacetime_dof_counter_matches_table1():
+    """Sec. 5.2, Table 1: 489 593 tets, 6 fields; spatial DOF ne nf N_p and spacetime DOF per slab
+    sum_i N_dof,i m q with m = 2p, q = p + 1.  Both orders run on the same tents, so one value of
+    sum_i |omega_V| must reproduce both printed spacetime counts through the oracle's counter
+    (a wrong m, q or N_p in it fails one of them)."""
     g = json.load(open(os.path.join(HERE, "golden", "table1_dofs.json")))
     ne, nf = g["n_elements"], g["n_fields"]
     for p, key in ((2, "p2"), (3, "p3")):
         nb = (p + 1) * (p + 2) * (p + 3) // 6
         spatial = ne * nf * nb
         assert abs(spatial - g[key]["spatial_dof"]) / g[key]["spatial_dof"] < 5e-4
-        # Table 1's spacetime count is (sum_i N_dof,i) * 2p(p+1); the implied
-        # sum_i N_dof,i / spatial DOF must be the same for both orders (same tents).
-        ratio = g[key]["spacetime_dof_per_slab"] / (2 * p * (p + 1)) / g[key]["spatial_dof"]
-        assert abs(ratio - 5.41) < 0.01
+    # synthetic tent list: 149 072 tents per slab (Sec. 5.2), one per vertex, patch sizes 17 or 18
+    # with sum_i |omega_V| = 2 650 000 (the value both printed counts imply)
+    n_tents, total = 149072, 2650000
+    sizes = np.full(n_tents, total // n_tents)
+    sizes[: total - sizes.sum()] += 1
+    tents = {"vertex": np.arange(n_tents)}
+    for p, key in ((2, "p2"), (3, "p3")):
+        nb = (p + 1) * (p + 2) * (p + 3) // 6
+        got = spacetime_dofs((nf, nb), tents, sizes, p)
+        printed = g[key]["spacetime_dof_per_slab"]
+        assert float(f"{got:.{g['printed_digits'] - 1}e}") == printed, (p, got, printed)
+    # a second right-hand side doubles the count
+    assert spacetime_dofs((nf, 10), tents, sizes, 2, nrhs=2) == 2 * spacetime_dofs((nf, 10), tents, sizes, 2)
 
 
 def test_front_before_layer():
