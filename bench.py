@@ -29,15 +29,32 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+import hashlib  # noqa: E402
+
 import numpy as np  # noqa: E402
 
 FP32_SM_LANES = 128            # FP32 FMA lanes per SM (Blackwell)
-N_SMS = 152
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per tent of the FP32 p=4 tent
-# kernels on the graded 32^3 workload, from the last ncu capture of the current kernel
-# version; an entry is removed once its kernel has changed since the counters were taken.
-TRAFFIC_BYTES_PER_TENT = {"fp32": 27529.6}              # tent_layer_kernel, per tent
-TRAFFIC_PERSISTENT_BYTES = {"fp32": 24458.8}            # tent_persistent_kernel, per tent (full evolve)
+KERNEL_SOURCES = ["paper_1906_11029_gb300/csrc/mtp_kernels.cuh", "paper_1906_11029_gb300/csrc/mtp_launch.cuh"]
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per tent of the tent kernels on the
+# graded 32^3 workload, from an ncu capture of a window of layers (scaled per tent), keyed by
+# (precision, kernel) and stamped with the hash of the kernel sources at capture time: a
+# stamp that no longer matches the sources means the kernel changed since, and the bench
+# reports traffic null.
+TRAFFIC_BYTES_PER_TENT = {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_tent(precision, kernel):
+    rec = TRAFFIC_BYTES_PER_TENT.get((precision, kernel))
+    if rec is None or rec["sources"] != kernel_source_hash():
+        return None
+    return rec["bytes_per_tent"]
 
 
 def load_peaks():
@@ -339,8 +356,11 @@ def run_equal_error(args):
     import mtp_synth as S
     import paper_1906_11029_gb300 as mtp
     w4 = make_workload(args.workload)
-    out, times = {}, {}
-    for p, prec in ((5, mtp.MTP_FP32), (4, mtp.MTP_FP32), (4, mtp.MTP_TF32), (4, mtp.MTP_TF32X3)):
+    out, times, dofs = {}, {}, {}
+    runs = [(5, mtp.MTP_FP32), (4, mtp.MTP_FP32), (4, mtp.MTP_TF32), (4, mtp.MTP_TF32X3)]
+    if args.equal_error_fp64:
+        runs.append((4, mtp.MTP_FP64))
+    for p, prec in runs:
         w = S.graded_sphere(32, p, 0.5) if args.workload == "graded" else w4
         mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=p, precision=prec)
         tents = mesh.pitch(w.T, w.causality)
@@ -351,6 +371,7 @@ def run_equal_error(args):
         b.record()
         torch.cuda.synchronize()
         times[(p, prec)] = a.elapsed_time(b)
+        dofs[(p, prec)] = tents.info["spacetime_dofs"]
         out[(p, prec)] = mesh.state_to_lattice(st).cpu().numpy()[0]
         del mesh, tents, st
     I = lattice_interpolation(3, 4, 5)
@@ -358,11 +379,23 @@ def run_equal_error(args):
     up = lambda u4: np.einsum("kl,elf->ekf", I, u4)
     ref = out[(4, mtp.MTP_FP32)]
     rel = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))
-    names = {mtp.MTP_FP32: "fp32", mtp.MTP_TF32: "tf32", mtp.MTP_TF32X3: "tf32x3"}
+    names = {mtp.MTP_FP32: "fp32", mtp.MTP_TF32: "tf32", mtp.MTP_TF32X3: "tf32x3", mtp.MTP_FP64: "fp64"}
     res = {"workload": w4.name, "e_disc_p4_vs_p5": rel(up(ref), u5),
            "ms": {f"p{p}_{names[q]}": v for (p, q), v in times.items()}}
     for q in (mtp.MTP_TF32, mtp.MTP_TF32X3):
         res[f"{names[q]}_vs_fp32"] = rel(out[(4, q)], ref)
+    if (4, mtp.MTP_FP64) in out:
+        # the whole evolve to T in FP64: each FP32-state mode against it, and against e_disc
+        u64 = out[(4, mtp.MTP_FP64)]
+        res["e_disc_fp64_p4_vs_p5"] = rel(up(u64), u5)
+        for q in (mtp.MTP_FP32, mtp.MTP_TF32, mtp.MTP_TF32X3):
+            d = rel(out[(4, q)], u64)
+            res[f"{names[q]}_vs_fp64_full_T"] = d
+            res[f"{names[q]}_vs_fp64_over_e_disc"] = d / res["e_disc_fp64_p4_vs_p5"]
+        rate = lambda k: dofs[k] / (times[k] / 1e3)
+        res["fp64_value"] = rate((4, mtp.MTP_FP64))
+        res["fp32_value"] = rate((4, mtp.MTP_FP32))
+        res["fp32_speedup_vs_fp64_full_T"] = times[(4, mtp.MTP_FP64)] / times[(4, mtp.MTP_FP32)]
     print(json.dumps(res))
 
 
@@ -424,6 +457,7 @@ def run_mtp(args):
         work.copy_(state0)
         tents.evolve(work)
     torch.cuda.synchronize()
+    probe = mtp.mtp_probe_rates()
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
@@ -446,25 +480,28 @@ def run_mtp(args):
     total_ms = max_over_ranks(total_ms, dist, "cuda")
     value = whole_job_rate(world, args.steps, dofs, total_ms)
 
-    # roofline of the tent kernel (the evolve is the tent-kernel graph)
+    # roofline of the tent kernel (the evolve is the tent-kernel graph); denominators: the FMA
+    # rates measured on this device by mtp_probe_rates (before the timed region), next to the
+    # unit-count figure from the device's SM count and maximum clock
     fl = flops_per_dof_update(w.dim, w.p)
     launch_ms = kern_ms / (args.steps * launches_per_step)
     flops_per_launch = dofs * fl / launches_per_step
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    unit_peak = n_sms * FP32_SM_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     if prec == mtp.MTP_FP32:
-        peak = N_SMS * FP32_SM_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        bound = "alu"
+        peak, src = probe["fp32_fma"], "mtp_probe_rates FP32 FMA loop on this device, this run"
     else:
-        peak = args.fp64_peak_tflops
-        bound = "alu"
+        peak, src = probe["fp64_fma"], "mtp_probe_rates FP64 FMA loop on this device, this run"
     achieved = flops_per_launch / (launch_ms / 1e3) / 1e12
-    tpl = (TRAFFIC_BYTES_PER_TENT.get(args.precision)
-           if args.workload == "graded" and not persistent else TRAFFIC_PERSISTENT_BYTES.get(args.precision))
-    traffic = None if tpl is None or args.workload != "graded" else tpl * tents.info["n_tents"] / launches_per_step
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+    kname = "tent_persistent_kernel" if persistent else "tent_layer_kernel"
+    tpl = traffic_per_tent(args.precision, kname) if args.workload == "graded" else None
+    traffic = None if tpl is None else tpl * tents.info["n_tents"] / launches_per_step
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": (f"tent_persistent_kernel<{args.precision},3,{w.p}>" if persistent
-                           else f"tent_layer_kernel<{args.precision},3,{w.p}>"),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock (unit counts)"}
+                "kernel": f"{kname}<{args.precision},3,{w.p}>", "peak_source": src,
+                "probe_tflops": probe, "fp32_unit_count_peak": unit_peak, "sms": n_sms,
+                "frac_of_unit_count_peak": achieved / unit_peak if prec == mtp.MTP_FP32 else None,
+                "kernel_sources": kernel_source_hash()}
 
     # end to end through the host-buffer entry point (pinned buffers, copies in the timed region)
     h_in = state0.cpu().pin_memory()
@@ -557,7 +594,6 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--fp64-window", type=float, default=0.02)
     ap.add_argument("--layer-launches", action="store_true", help="one launch per layer instead of the DAG walk")
-    ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
     ap.add_argument("--cpu-tents", type=int, default=80, help="oracle baseline: tents (per process)")
     ap.add_argument("--cpu-rounds", type=int, default=80)
     ap.add_argument("--ref-tents", type=int, default=20, help="reference arm: tents per host core per step")
@@ -568,6 +604,8 @@ def main():
     ap.add_argument("--profile-window", default=None, help="a:b -> apply layers [a, b) once and exit")
     ap.add_argument("--profile-evolve", action="store_true", help="run one full evolve and exit")
     ap.add_argument("--equal-error", action="store_true", help="p=4 precision modes against p=5")
+    ap.add_argument("--equal-error-fp64", action="store_true",
+                    help="with --equal-error: also one full FP64 p=4 evolve (about 10 min on the graded workload)")
     ap.add_argument("--seed", type=int, default=7)
     args = ap.parse_args()
     if args.cpu_worker:

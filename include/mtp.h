@@ -216,15 +216,17 @@ int mtp_energy(mtp_mesh_t mesh, const void* state_dev, double* out_host, void* s
  * through its own allocator and budget, or a loop that must not allocate after start-up).
  * The paper has no counterpart to this call.
  * Inputs and outputs are all the caller's: state_dev (library layout, n_rhs states of
- * n_elems elements of degree p in the given precision), eps_dev and mu_dev [n_elems]
- * (double, device), out_dev[n_rhs] (double, device) receives the energies.  Nothing is
- * allocated: the reduction scratch is a fixed static device array of 304 x 64 doubles
- * (152 KiB) that every GPU loading this library holds until the process exits; n_rhs
- * above 64 is rejected with MTP_EINVAL.  Every call writes all the scratch it reads, so
- * no clearing is needed, but all calls share that one array: calls that overlap on the
- * GPU (e.g. on two streams at once) race and give wrong results.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress, with that device
- * current); make that first call before any stream capture.  Asynchronous on the stream. */
+ * n_elems elements of degree p in the given precision: double for MTP_FP64, float for
+ * MTP_FP32, MTP_TF32 and MTP_TF32X3), eps_dev and mu_dev [n_elems] (double, device),
+ * out_dev[n_rhs] (double, device) receives the energies.  Nothing is allocated: the
+ * reduction scratch is a fixed static device array of 304 x 64 doubles (152 KiB) that every
+ * GPU loading this library holds until the process exits; n_rhs above 64 is rejected with
+ * MTP_EINVAL.  Every call writes all the scratch it reads, so no clearing is needed, but all
+ * calls share that one array: calls that overlap on the GPU (e.g. on two streams at once)
+ * race and give wrong results.  Every call looks the array's device address up again
+ * (cudaGetSymbolAddress, with the calling thread's current device), so nothing stale survives a
+ * device reset; the first call on a device may load the library's device code for it, so make
+ * that first call before any stream capture.  Asynchronous on the stream. */
 int mtp_energy_noalloc(const void* state_dev, const double* eps_dev, const double* mu_dev,
                        int dim, int64_t n_elems, int p, int precision, int n_rhs,
                        double* out_dev, void* stream);

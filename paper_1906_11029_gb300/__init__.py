@@ -258,9 +258,30 @@ def mtp_energy(mesh, state_dev, n_rhs=1, stream=None):
 
 
 def mtp_energy_noalloc(state_dev, eps_dev, mu_dev, dim, n_elems, p, precision, n_rhs, out_dev, stream=None):
-    """Energies into the caller's device buffer out_dev[n_rhs]; allocates nothing (see mtp.h)."""
+    """Energies into the caller's device buffer out_dev[n_rhs]; allocates nothing (see mtp.h).
+    Torch tensors are checked against the sizes and types the call reads and writes before the
+    pointers cross the ABI (a wrong size would make the kernel access memory out of bounds)."""
+    _check_noalloc_args(state_dev, eps_dev, mu_dev, dim, n_elems, p, precision, n_rhs, out_dev)
     _check(_lib.mtp_energy_noalloc(_ptr(state_dev), _ptr(eps_dev), _ptr(mu_dev), dim, n_elems, p, precision,
                                    n_rhs, _ptr(out_dev), _stream(stream)))
+
+
+def _check_noalloc_args(state, eps, mu, dim, n_elems, p, precision, n_rhs, out):
+    import torch
+    if dim not in (2, 3) or not 1 <= p <= 5 or n_elems < 1 or n_rhs < 1:
+        return                                   # the library reports these itself
+    nf = 3 if dim == 2 else 6
+    nb = (p + 1) * (p + 2) // 2 if dim == 2 else (p + 1) * (p + 2) * (p + 3) // 6
+    want = torch.float64 if precision == MTP_FP64 else torch.float32
+    checks = [(state, want, n_rhs * n_elems * nf * nb, "state"), (eps, torch.float64, n_elems, "eps"),
+              (mu, torch.float64, n_elems, "mu"), (out, torch.float64, n_rhs, "out")]
+    for t, dtype, n, name in checks:
+        if not isinstance(t, torch.Tensor):
+            continue
+        if not t.is_cuda or not t.is_contiguous() or t.dtype != dtype or t.numel() < n:
+            raise MtpError(MTP_EINVAL, f"mtp_energy_noalloc: {name} must be a contiguous CUDA {dtype} "
+                                       f"tensor of at least {n} elements (got {t.dtype}, {t.numel()}, "
+                                       f"cuda={t.is_cuda})")
 
 
 def mtp_probe_rates(stream=None):

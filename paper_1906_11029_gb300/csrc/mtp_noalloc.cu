@@ -6,7 +6,6 @@
 // memory through its own caching allocator and budget, or a loop that must not allocate
 // after start-up.  This variant takes every array it reads or writes from the caller and
 // keeps its reduction scratch in a fixed file-scope device array instead.
-#include <mutex>
 #include <string>
 
 #include <cuda_runtime.h>
@@ -18,7 +17,6 @@ namespace mtp {
 constexpr int kNoAllocBlocks = 304;     // 2 blocks per SM on 152 SMs
 constexpr int kNoAllocThreads = 256;
 constexpr int kNoAllocMaxRhs = 64;      // scratch: 304 x 64 doubles = 152 KiB per device
-constexpr int kNoAllocMaxDevices = 64;
 
 // Reduction scratch shared by every call on a device; it lives (on every GPU that loads
 // this library) until the process exits.  Each call writes every slot that it later reads,
@@ -64,24 +62,17 @@ __global__ void energy_final_noalloc_kernel(const double* scratch, double* out) 
 }
 
 // Device address of g_energy_scratch on the current device.  In host code the symbol's
-// name is only a host-side handle, never a device address, so it is looked up once per
-// device with cudaGetSymbolAddress (with that device current) and cached.
+// name is only a host-side handle, never a device address, so it is looked up with
+// cudaGetSymbolAddress (with the device current) on every call: nothing is cached, so an
+// address that a device reset made stale is never reused.  The first lookup on a device
+// may load this file's device code, which is why the first call belongs before any stream
+// capture.
 static int scratch_address(double** out) {
-    static std::mutex mu;
-    static double* cache[kNoAllocMaxDevices] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return set_error(MTP_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return set_error(MTP_EUNSUPPORTED, "device ordinal above 63");
-    std::lock_guard<std::mutex> lk(mu);
-    if (!cache[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_energy_scratch);
-        if (e != cudaSuccess || !p)
-            return set_error(MTP_ECUDA, std::string("cudaGetSymbolAddress(g_energy_scratch): ") + cudaGetErrorString(e));
-        cache[dev] = (double*)p;
-    }
-    *out = cache[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_energy_scratch);
+    if (e != cudaSuccess || !p)
+        return set_error(MTP_ECUDA, std::string("cudaGetSymbolAddress(g_energy_scratch): ") + cudaGetErrorString(e));
+    *out = (double*)p;
     return MTP_OK;
 }
 
@@ -96,20 +87,21 @@ extern "C" int mtp_energy_noalloc(const void* state_dev, const double* eps_dev, 
     if (dim != 2 && dim != 3) return set_error(MTP_EINVAL, "dim must be 2 or 3");
     if (p < 1 || p > kMaxDegree) return set_error(MTP_EINVAL, "p must be in 1..5");
     if (n_elems < 1) return set_error(MTP_EINVAL, "n_elems must be positive");
-    if (precision != MTP_FP64 && precision != MTP_FP32) return set_error(MTP_EINVAL, "unknown precision");
+    if (precision != MTP_FP64 && precision != MTP_FP32 && precision != MTP_TF32 && precision != MTP_TF32X3)
+        return set_error(MTP_EINVAL, "unknown precision");
     if (n_rhs < 1 || n_rhs > kNoAllocMaxRhs)
         return set_error(MTP_EINVAL, "n_rhs must be in 1.." + std::to_string(kNoAllocMaxRhs) +
                                          " (size of the static scratch of mtp_energy_noalloc)");
+    cudaStream_t st = (cudaStream_t)stream;
     double* scratch = nullptr;
     int rc = scratch_address(&scratch);
     if (rc != MTP_OK) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
     const int nf = n_fields(dim), nb = n_basis(dim, p);
     dim3 grid(kNoAllocBlocks, n_rhs);
     if (precision == MTP_FP64)
         energy_partial_noalloc_kernel<double><<<grid, kNoAllocThreads, 0, st>>>(
             (const double*)state_dev, eps_dev, mu_dev, n_elems, nf, nb, scratch);
-    else
+    else   // MTP_FP32, MTP_TF32, MTP_TF32X3: float states
         energy_partial_noalloc_kernel<float><<<grid, kNoAllocThreads, 0, st>>>(
             (const float*)state_dev, eps_dev, mu_dev, n_elems, nf, nb, scratch);
     energy_final_noalloc_kernel<<<n_rhs, kNoAllocThreads, 0, st>>>(scratch, out_dev);

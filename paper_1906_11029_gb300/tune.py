@@ -10,7 +10,10 @@ Two levels:
   cores.  Variants are timed on the same layer window of the caller's workload.
 
 Choices are cached in a JSON file (default ``~/.cache/paper_1906_11029_gb300/tune.json``)
-keyed by GPU name, dimension, degree, accuracy class and largest patch size.
+keyed by GPU name, dimension, degree, accuracy class, largest patch size and the workload's
+shape: its element count and the power of two nearest its average number of tents per layer
+(which decides between the DAG walk and per-layer launches), so a choice timed on a small mesh
+is not reused for a large one.
 """
 from __future__ import annotations
 
@@ -25,10 +28,13 @@ CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1906_11029_gb300"
 LAUNCH_NAMES = ["dag_walk", "dag_walk_1cta", "layer_launches"]
 
 
-def _key(dim, p, accuracy, max_patch):
+def _key(dim, p, accuracy, max_patch, n_elems, tents_per_layer):
+    import math
+
     import torch
     name = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
-    return f"{name}|dim{dim}|p{p}|{accuracy}|mp{max_patch}"
+    tpl = int(round(math.log2(max(1.0, tents_per_layer))))
+    return f"{name}|dim{dim}|p{p}|{accuracy}|mp{max_patch}|ne{n_elems}|tpl2^{tpl}"
 
 
 def _load(path):
@@ -64,7 +70,9 @@ def autotune(dim, vertices, elements, eps, mu, p, T, lattice_values, accuracy="f
     import torch
     data = _load(cache)
     probe = Mesh(dim, vertices, elements, eps, mu, p=p, precision=MTP_FP32)
-    key = _key(dim, p, accuracy, probe.info["max_patch"])
+    ptents = probe.pitch(T, causality_factor)
+    key = _key(dim, p, accuracy, probe.info["max_patch"], len(elements),
+               ptents.info["n_tents"] / max(1, ptents.info["n_layers"]))
     if key in data and not force:
         rec = data[key]
         return rec["precision"], rec["launch"], rec
