@@ -399,6 +399,35 @@ def run_equal_error(args):
     print(json.dumps(res))
 
 
+def adjoint_timing(reps=3):
+    """The adjoint workload (8^3 x 6 tets, p = 2, eps ~ U[1, 3] seeded, T = 0.5, FP64, tents
+    pitched for wave speed 1): milliseconds of one forward evolve and of one mtp_adjoint (forward
+    pass with checkpoints, recomputation with the compact patch tape, reverse sweep), best of
+    `reps` after a warm-up."""
+    import torch
+    import mtp_synth as S
+    import paper_1906_11029_gb300 as mtp
+    w = S.adjoint_cube(8, 2, 0.5)
+    m = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=w.p)
+    t = m.pitch(w.T, 0.5, wavespeed=np.ones(len(w.elems)))
+    st0 = m.state_from_lattice(torch.tensor(initial_lattice(w)[None], device="cuda"))
+    lamT = torch.randn_like(st0)
+    lam0 = torch.empty_like(st0)
+    ge = torch.empty(len(w.elems), dtype=torch.float64, device="cuda")
+    gm = torch.empty_like(ge)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fw, ad = [], []
+    for r in range(reps + 1):
+        x = st0.clone()
+        a.record(); t.evolve(x); b.record(); torch.cuda.synchronize()
+        fw.append(a.elapsed_time(b))
+        a.record(); mtp.mtp_adjoint(t.h, st0, lamT, lam0, ge, gm); b.record(); torch.cuda.synchronize()
+        ad.append(a.elapsed_time(b))
+    f, g = min(fw[1:]), min(ad[1:])
+    return {"workload": w.name, "layers": t.info["n_layers"], "tents": t.info["n_tents"], "forward_ms": f,
+            "adjoint_ms": g, "adjoint_over_forward": g / f}
+
+
 def max_over_ranks(ms, dist, device):
     """The slowest rank's time (every rank gets it); `dist` None for one process."""
     import torch
@@ -550,6 +579,8 @@ def run_mtp(args):
                 "rel_l2_vs_fp64_on_window": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64))}
         del mesh64, tents64, s64, s64w
 
+    adj = adjoint_timing() if rank == 0 and not args.no_adjoint else None
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cores = min(host_cores(), args.cpu_max_procs)
@@ -575,7 +606,7 @@ def run_mtp(args):
                        "l2": "state larger than L2 (%.0f MB)" % (state0.numel() * state0.element_size() / 1e6),
                        "pitch_s": t2 - t1, "pitch_device_s": t3 - t2, "mesh_s": t1 - t0},
             "clocks": clk, "gpu_launches": launches_per_step * args.steps,
-            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "fp64_gpu": fp64,
+            "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu, "fp64_gpu": fp64, "adjoint": adj,
             "peaks": peak_kind,
         }
         print(json.dumps(line))
@@ -600,6 +631,7 @@ def main():
     ap.add_argument("--cpu-procs", type=int, default=1, help="oracle worker: processes over the tents of a layer")
     ap.add_argument("--cpu-max-procs", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint timing extra")
     ap.add_argument("--cpu-worker", default=None)
     ap.add_argument("--profile-window", default=None, help="a:b -> apply layers [a, b) once and exit")
     ap.add_argument("--profile-evolve", action="store_true", help="run one full evolve and exit")

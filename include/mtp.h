@@ -18,8 +18,8 @@
  *     Device work is enqueued on that stream; calls return when it is enqueued
  *     unless stated otherwise.
  *   - State layout ("library layout"): state[r][e][f][a], r < n_rhs, e < n_elems,
- *     f < n_fields, a < n_basis, in the mesh's precision (double for MTP_FP64, float
- *     for the others).  The coefficients are those of the conserved variable
+ *     f < n_fields, a < n_basis, in the mesh's state precision (double for MTP_FP64 and
+ *     MTP_FP32_SPLIT, float for the others).  The coefficients are those of the conserved variable
  *     y = g(u) - f(u) grad(phi) (Sec. 3, transformed equation; y = (eps E, mu H) on
  *     a flat front) in an L2-orthonormal basis of P_p on each element.
  *   - Lattice layout: vals[r][e][k][f] in double, the value of y at lattice point k
@@ -63,6 +63,12 @@ extern "C" {
                           with TF32 operands and FP32 accumulation */
 #define MTP_TF32X3 3   /* 3D: as MTP_TF32 with each operand split into TF32 hi + lo parts and
                           three products (hi*hi + hi*lo + lo*hi), about FP32 accuracy */
+#define MTP_FP32_SPLIT 4 /* FP32 operator arithmetic (as MTP_FP32); the Taylor sum of each tent
+                          (Sec. 4, eq. recursion-init) is carried as an unevaluated FP32 pair
+                          hi + lo updated by error-free two-sum, and the state between tents is
+                          stored in FP64 (library layout in double).  Removes the rounding of the
+                          accumulation and of the stored state, the dominant FP32 error terms.
+                          Not available for batches or the adjoint. */
 
 typedef struct mtp_mesh*  mtp_mesh_t;
 typedef struct mtp_tents* mtp_tents_t;
@@ -72,7 +78,7 @@ typedef struct {
     int p;          /* polynomial degree of V_h, 1..5 (Sec. 3, DG space)                   */
     int q;          /* SAT stages; 0 selects p+1 (Sec. 5.1)                                */
     int m;          /* SAT sub-intervals per tent; 0 selects 2p (Sec. 5.1)                 */
-    int precision;  /* MTP_FP64, MTP_FP32, MTP_TF32 or MTP_TF32X3                            */
+    int precision;  /* MTP_FP64, MTP_FP32, MTP_TF32, MTP_TF32X3 or MTP_FP32_SPLIT            */
     int n_rhs;      /* independent states evolved with the same tents (>= 1; 0 means 1)   */
     int flags;      /* MTP_FLAG_* bits; 0 by default                                       */
 } mtp_options;
@@ -216,8 +222,8 @@ int mtp_energy(mtp_mesh_t mesh, const void* state_dev, double* out_host, void* s
  * through its own allocator and budget, or a loop that must not allocate after start-up).
  * The paper has no counterpart to this call.
  * Inputs and outputs are all the caller's: state_dev (library layout, n_rhs states of
- * n_elems elements of degree p in the given precision: double for MTP_FP64, float for
- * MTP_FP32, MTP_TF32 and MTP_TF32X3), eps_dev and mu_dev [n_elems] (double, device),
+ * n_elems elements of degree p in the given precision: double for MTP_FP64 and
+ * MTP_FP32_SPLIT, float for MTP_FP32, MTP_TF32 and MTP_TF32X3), eps_dev and mu_dev [n_elems] (double, device),
  * out_dev[n_rhs] (double, device) receives the energies.  Nothing is allocated: the
  * reduction scratch is a fixed static device array of 304 x 64 doubles (152 KiB) that every
  * GPU loading this library holds until the process exits; n_rhs above 64 is rejected with

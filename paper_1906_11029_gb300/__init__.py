@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(HERE, "_lib", "libmtp.so")
 
 MTP_OK, MTP_EINVAL, MTP_EMESH, MTP_ECAUSAL = 0, -1, -2, -3
 MTP_ENOMEM, MTP_ECUDA, MTP_ETIMEOUT, MTP_ENUMERIC, MTP_EUNSUPPORTED = -4, -5, -6, -7, -8
-MTP_FP64, MTP_FP32, MTP_TF32, MTP_TF32X3 = 0, 1, 2, 3
+MTP_FP64, MTP_FP32, MTP_TF32, MTP_TF32X3, MTP_FP32_SPLIT = 0, 1, 2, 3, 4
 MTP_FLAG_LAYER_LAUNCHES, MTP_FLAG_TEST_STALL = 1, 2
 _CODES = {0: "MTP_OK", -1: "MTP_EINVAL", -2: "MTP_EMESH", -3: "MTP_ECAUSAL", -4: "MTP_ENOMEM",
           -5: "MTP_ECUDA", -6: "MTP_ETIMEOUT", -7: "MTP_ENUMERIC", -8: "MTP_EUNSUPPORTED"}
@@ -272,7 +272,7 @@ def _check_noalloc_args(state, eps, mu, dim, n_elems, p, precision, n_rhs, out):
         return                                   # the library reports these itself
     nf = 3 if dim == 2 else 6
     nb = (p + 1) * (p + 2) // 2 if dim == 2 else (p + 1) * (p + 2) * (p + 3) // 6
-    want = torch.float64 if precision == MTP_FP64 else torch.float32
+    want = torch.float64 if precision in (MTP_FP64, MTP_FP32_SPLIT) else torch.float32
     checks = [(state, want, n_rhs * n_elems * nf * nb, "state"), (eps, torch.float64, n_elems, "eps"),
               (mu, torch.float64, n_elems, "mu"), (out, torch.float64, n_rhs, "out")]
     for t, dtype, n, name in checks:
@@ -314,7 +314,7 @@ class Mesh:
 
     def torch_dtype(self):
         import torch
-        return torch.float64 if self.precision == MTP_FP64 else torch.float32
+        return torch.float64 if self.precision in (MTP_FP64, MTP_FP32_SPLIT) else torch.float32
 
     def new_state(self, device="cuda"):
         import torch

@@ -78,7 +78,7 @@ template <typename Real, int DIM, int P>
 struct AdjLayout {
     SmemLayout<Real, DIM, P> base;
     size_t off_lam, off_nu, off_ly, off_up, off_trU, off_g, bytes;
-    __host__ __device__ explicit AdjLayout(int mp) : base(mp) {
+    __host__ __device__ explicit AdjLayout(int mp) : base(mp, 0, true) {
         size_t o = base.bytes;
         off_lam = o; o = base.align16(o + base.state_bytes);
         off_nu = o; o = base.align16(o + base.state_bytes);

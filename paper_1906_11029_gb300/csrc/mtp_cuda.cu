@@ -31,7 +31,8 @@ struct DeviceMesh {
     void* S = nullptr;
     void* Tr = nullptr;
     void* L = nullptr;
-    void* Sc = nullptr;           // thread-major copies of S, Tr, L for the SIMT tent kernels
+    void* Mc = nullptr;           // thread-major copies of M, D^T, Tr, L for the SIMT tent kernels
+    void* Dc = nullptr;
     void* Trc = nullptr;
     void* Lc = nullptr;
     double* V = nullptr;
@@ -68,12 +69,16 @@ struct DeviceTents {
     void* adj_buf = nullptr;
     size_t adj_bytes = 0;
     double* tau_rev = nullptr;
+    int64_t* tent_off = nullptr;   // [n_tents + 1]: patch entries of the tents before each tent
 };
 
 constexpr int kEnergyBlocks = 304;
 constexpr int kEnergyThreads = 256;
 
-static size_t real_size(const Mesh& m) { return m.precision == MTP_FP64 ? sizeof(double) : sizeof(float); }
+// the state between tents is FP64 for MTP_FP64 and MTP_FP32_SPLIT, FP32 otherwise; the reference
+// tables and the tent kernels' arithmetic are FP64 only for MTP_FP64
+static bool state_f64(const Mesh& m) { return m.precision == MTP_FP64 || m.precision == MTP_FP32_SPLIT; }
+static size_t real_size(const Mesh& m) { return state_f64(m) ? sizeof(double) : sizeof(float); }
 
 template <typename T>
 static int upload(T** dst, const T* src, size_t n) {
@@ -113,7 +118,7 @@ static std::vector<double> thread_major(const std::vector<double>& src, int nmat
 }
 
 static int upload_real(const Mesh& m, void** dst, const std::vector<double>& src) {
-    if (m.precision == MTP_FP64) return upload((double**)dst, src.data(), src.size());
+    if (m.precision == MTP_FP64) return upload((double**)dst, src.data(), src.size());   // FP32 arithmetic otherwise
     std::vector<float> f(src.begin(), src.end());
     return upload((float**)dst, f.data(), f.size());
 }
@@ -173,7 +178,15 @@ int device_mesh_upload(Mesh& m) {
     MTP_TRY(upload_real(m, &d.L, pad_rows(m.ref.L, m.nfb)));    // [j][f][a][NFBP]
     {
         const int w = m.precision == MTP_FP64 ? 2 : 4, ap = 2, nv = m.dim + 1;
-        MTP_TRY(upload_real(m, &d.Sc, thread_major(m.ref.S, nv * m.dim, m.nb, m.nb, w, ap)));
+        // factored volume: M[j] (rows c < nbm, columns b) and D[l]^T (rows a, columns c < nbm)
+        const int nbm = m.ref.nbm;
+        std::vector<double> Dt((size_t)m.dim * m.nb * nbm);
+        for (int l = 0; l < m.dim; ++l)
+            for (int c = 0; c < nbm; ++c)
+                for (int a = 0; a < m.nb; ++a)
+                    Dt[((size_t)l * m.nb + a) * nbm + c] = m.ref.D[((size_t)l * nbm + c) * m.nb + a];
+        MTP_TRY(upload_real(m, &d.Mc, thread_major(m.ref.M, nv, nbm, m.nb, w, ap)));
+        MTP_TRY(upload_real(m, &d.Dc, thread_major(Dt, m.dim, m.nb, nbm, w, ap)));
         MTP_TRY(upload_real(m, &d.Trc, thread_major(m.ref.Tr, nv, m.nfb, m.nb, w, ap)));
         MTP_TRY(upload_real(m, &d.Lc, thread_major(m.ref.L, nv * nv, m.nb, m.nfb, w, ap)));
     }
@@ -212,7 +225,7 @@ int device_mesh_upload(Mesh& m) {
 void device_mesh_free(Mesh& m) {
     if (!m.dev) return;
     DeviceMesh& d = *m.dev;
-    void* ptrs[] = {d.geo, d.elems, d.patch_ptr, d.patch_elem, d.patch_info, d.S, d.Tr, d.L, d.Sc, d.Trc, d.Lc,
+    void* ptrs[] = {d.geo, d.elems, d.patch_ptr, d.patch_elem, d.patch_info, d.S, d.Tr, d.L, d.Mc, d.Dc, d.Trc, d.Lc,
                     d.V, d.Vinv, d.partial,
                     d.Sf, d.Lfr, d.Trf, d.Sf_lo, d.Lfr_lo, d.Trf_lo};
     for (void* p : ptrs)
@@ -226,7 +239,7 @@ void device_tents_free(Tents& t) {
     DeviceTents& d = *t.dev;
     if (d.exec) cudaGraphExecDestroy(d.exec);
     if (d.capture) cudaStreamDestroy(d.capture);
-    void* ptrs[] = {d.v, d.tb, d.tt, d.tau, d.err, d.host_state, d.adj_buf, d.tau_rev, d.tent_layer, d.vt_ptr,
+    void* ptrs[] = {d.v, d.tb, d.tt, d.tau, d.err, d.host_state, d.adj_buf, d.tau_rev, d.tent_off, d.tent_layer, d.vt_ptr,
                     d.vt_layer, d.adj_ptr, d.adj, d.cnt, d.next};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -268,14 +281,16 @@ static int device_tents_upload(Tents& t) {
 }
 
 static const KernelEntry& kernel_entry(const Mesh& m) {
-    static KernelEntry f64[2][5], f32[2][5], tc[2][5];
+    static KernelEntry f64[2][5], f32[2][5], tc[2][5], split[2][5];
     static bool init = false;
     if (!init) {
         kernel_table_f64(f64);
         kernel_table_f32(f32);
         kernel_table_tc(tc);
+        kernel_table_split(split);
         init = true;
     }
+    if (m.precision == MTP_FP32_SPLIT) return split[m.dim - 2][m.p - 1];
     if (m.precision == MTP_TF32 || m.precision == MTP_TF32X3)
         return tc[m.precision == MTP_TF32 ? 0 : 1][m.p - 1];
     return (m.precision == MTP_FP64 ? f64 : f32)[m.dim - 2][m.p - 1];
@@ -330,7 +345,7 @@ int device_from_lattice(Mesh& m, const double* vals, void* state, void* stream) 
     MTP_TRY(device_mesh_upload(m));
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = (int64_t)m.n_rhs * m.ne * m.nb;
-    if (m.precision == MTP_FP64)
+    if (state_f64(m))
         from_lattice_kernel<double><<<grid_for(n, 256), 256, 0, st>>>(vals, (double*)state, m.dev->geo, m.dev->Vinv,
                                                                        m.ne, m.nf, m.nb, m.n_rhs);
     else
@@ -344,7 +359,7 @@ int device_to_lattice(Mesh& m, const void* state, double* vals, void* stream) {
     MTP_TRY(device_mesh_upload(m));
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n = (int64_t)m.n_rhs * m.ne * m.nb;
-    if (m.precision == MTP_FP64)
+    if (state_f64(m))
         to_lattice_kernel<double><<<grid_for(n, 256), 256, 0, st>>>((const double*)state, vals, m.dev->geo, m.dev->V,
                                                                      m.ne, m.nf, m.nb, m.n_rhs);
     else
@@ -401,7 +416,7 @@ int device_energy(Mesh& m, const void* state, double* out_host, void* stream) {
     MTP_TRY(device_mesh_upload(m));
     cudaStream_t st = (cudaStream_t)stream;
     dim3 grid(kEnergyBlocks, m.n_rhs);
-    if (m.precision == MTP_FP64)
+    if (state_f64(m))
         energy_partial_kernel<double><<<grid, kEnergyThreads, 0, st>>>((const double*)state, m.dev->geo, m.ne, m.nf,
                                                                         m.nb, m.dev->partial);
     else
@@ -436,7 +451,8 @@ static void fill_args(Tents& t, void* state, KArgs& a) {
     a.S = dm.S;
     a.Tr = dm.Tr;
     a.L = dm.L;
-    a.Sc = dm.Sc;
+    a.Mc = dm.Mc;
+    a.Dc = dm.Dc;
     a.Trc = dm.Trc;
     a.Lc = dm.Lc;
     a.Sf = (const float4*)dm.Sf;
@@ -579,9 +595,59 @@ int device_evolve_host(Tents& t, const void* in, void* out, void* stream) {
 
 namespace mtp {
 
+// Patch tape of one layer: the coefficients of the elements of every tent's patch, tents in
+// layer order, each patch's elements in patch order; entry e of the tape holds nc = n_fields
+// x n_basis values per right-hand side, tape[rhs][e][nc].  One block per (tent, rhs).
+template <typename Real, bool GATHER>
+__global__ void patch_tape_kernel(Real* state, Real* tape, const int32_t* tent_v, const int64_t* tent_off,
+                                  const int64_t* patch_ptr, const int32_t* patch_elem, int64_t t0, int64_t e0,
+                                  int nc, int64_t state_rhs_stride, int64_t tape_rhs_stride) {
+    const int64_t t = t0 + blockIdx.x;
+    const int V = tent_v[t];
+    const int64_t pb = patch_ptr[V], ns = patch_ptr[V + 1] - pb;
+    Real* st = state + (int64_t)blockIdx.y * state_rhs_stride;
+    Real* tp = tape + (int64_t)blockIdx.y * tape_rhs_stride + (tent_off[t] - e0) * nc;
+    for (int64_t i = threadIdx.x; i < ns * nc; i += blockDim.x) {
+        const int64_t k = i / nc, r = i - k * nc;
+        Real* g = st + (int64_t)patch_elem[pb + k] * nc + r;
+        if (GATHER) tp[i] = *g; else *g = tp[i];
+    }
+}
+
+static int patch_tape(Tents& t, void* state, void* tape, int64_t layer, int64_t e0, int64_t tape_entries,
+                      bool gather, cudaStream_t st) {
+    Mesh& m = *t.mesh;
+    const int64_t t0 = t.layer_ptr[layer], n = t.layer_ptr[layer + 1] - t0;
+    if (n == 0) return MTP_OK;
+    const int nc = m.nf * m.nb;
+    dim3 grid((unsigned)n, m.n_rhs);
+    const int64_t srs = m.ne * nc, trs = tape_entries * nc;
+    DeviceMesh& dm = *m.dev;
+    DeviceTents& d = *t.dev;
+    if (m.precision == MTP_FP64) {
+        if (gather)
+            patch_tape_kernel<double, true><<<grid, 128, 0, st>>>((double*)state, (double*)tape, d.v, d.tent_off,
+                                                                  dm.patch_ptr, dm.patch_elem, t0, e0, nc, srs, trs);
+        else
+            patch_tape_kernel<double, false><<<grid, 128, 0, st>>>((double*)state, (double*)tape, d.v, d.tent_off,
+                                                                   dm.patch_ptr, dm.patch_elem, t0, e0, nc, srs, trs);
+    } else {
+        if (gather)
+            patch_tape_kernel<float, true><<<grid, 128, 0, st>>>((float*)state, (float*)tape, d.v, d.tent_off,
+                                                                 dm.patch_ptr, dm.patch_elem, t0, e0, nc, srs, trs);
+        else
+            patch_tape_kernel<float, false><<<grid, 128, 0, st>>>((float*)state, (float*)tape, d.v, d.tent_off,
+                                                                  dm.patch_ptr, dm.patch_elem, t0, e0, nc, srs, trs);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return MTP_OK;
+}
+
 // Reverse sweep with layer checkpointing: the forward pass keeps the state before every
-// K-th layer; each segment is recomputed from its checkpoint (keeping the state before each
-// of its layers) and then reversed layer by layer with the adjoint tent kernel.
+// K-th layer; each segment is recomputed from its checkpoint, saving before each of its
+// layers only the patch elements that layer touches (a compact patch tape), and is then
+// reversed layer by layer: the layer's patch tape is scattered into a work state and the
+// adjoint tent kernel reads its bottom values there.
 int device_adjoint(Tents& t, const void* state0, const void* lamT, void* lam0, double* geps, double* gmu,
                    int64_t K, void* stream) {
     MTP_TRY(device_tents_upload(t));
@@ -591,6 +657,8 @@ int device_adjoint(Tents& t, const void* state0, const void* lamT, void* lam0, d
     static AdjEntry table[2][2][5];
     static bool init = false;
     if (!init) { adjoint_table(table); init = true; }
+    if (m.precision == MTP_FP32_SPLIT)
+        return set_error(MTP_EUNSUPPORTED, "the adjoint runs FP64, FP32 and tensor-core meshes, not MTP_FP32_SPLIT");
     const AdjEntry& ae = table[m.precision == MTP_FP64 ? 0 : 1][m.dim - 2][m.p - 1];
     const KernelEntry& ke = kernel_entry(m);
     size_t smem = 0, smem_f = 0;
@@ -612,9 +680,21 @@ int device_adjoint(Tents& t, const void* state0, const void* lamT, void* lam0, d
     const size_t sbytes = (size_t)m.n_rhs * m.ne * m.nf * m.nb * real_size(m);
     int64_t max_tents = 0;
     for (int64_t l = 0; l < nl; ++l) max_tents = std::max(max_tents, t.layer_ptr[l + 1] - t.layer_ptr[l]);
+    // patch entries before each tent; the largest segment's patch tape
+    std::vector<int64_t> off(t.vertex.size() + 1, 0);
+    for (size_t i = 0; i < t.vertex.size(); ++i)
+        off[i + 1] = off[i] + (m.patch_ptr[t.vertex[i] + 1] - m.patch_ptr[t.vertex[i]]);
+    if (!d.tent_off) MTP_TRY(upload(&d.tent_off, off.data(), off.size()));
+    int64_t seg_entries = 0;
+    for (int64_t c = 0; c < nck; ++c) {
+        const int64_t l0 = c * K, l1 = std::min((c + 1) * K, nl);
+        seg_entries = std::max(seg_entries, off[t.layer_ptr[l1]] - off[t.layer_ptr[l0]]);
+    }
+    const size_t ptape_bytes = (size_t)seg_entries * m.n_rhs * m.nf * m.nb * real_size(m);
     const int64_t tstride = ae.tape_stride(m.max_patch, m.m, m.q);
     const size_t tape_bytes = (size_t)max_tents * m.n_rhs * tstride * real_size(m);
-    const size_t need = (size_t)(nck + K) * sbytes + tape_bytes + 256;
+    auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t need = align((size_t)(nck + 2) * sbytes) + align(ptape_bytes) + tape_bytes + 256;
     if (d.adj_bytes < need) {
         if (d.adj_buf) cudaFree(d.adj_buf);
         d.adj_buf = nullptr;
@@ -623,21 +703,21 @@ int device_adjoint(Tents& t, const void* state0, const void* lamT, void* lam0, d
         d.adj_bytes = need;
     }
     if (!d.tau_rev) CUDA_TRY(cudaMalloc((void**)&d.tau_rev, sizeof(double) * m.nv));
-    auto align = [](size_t x) { return (x + 255) & ~size_t(255); };
     char* base = (char*)d.adj_buf;
     auto ckpt = [&](int64_t c) { return (void*)(base + c * sbytes); };
-    char* segb = base + nck * sbytes;
-    auto seg = [&](int64_t s) { return (void*)(segb + s * sbytes); };
-    void* tape = (void*)(base + align((size_t)(nck + K) * sbytes));
+    void* work = (void*)(base + nck * sbytes);          // the recomputed state
+    void* ybot = (void*)(base + (nck + 1) * sbytes);    // bottom values of the layer being reversed
+    void* ptape = (void*)(base + align((size_t)(nck + 2) * sbytes));
+    void* tape = (void*)(base + align((size_t)(nck + 2) * sbytes) + align(ptape_bytes));
 
     CUDA_TRY(cudaMemsetAsync(d.err, 0, sizeof(int), st));
     // forward pass with checkpoints
     MTP_TRY(set_front(t, 0, d.tau, st));
-    CUDA_TRY(cudaMemcpyAsync(seg(0), state0, sbytes, cudaMemcpyDeviceToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(work, state0, sbytes, cudaMemcpyDeviceToDevice, st));
     KArgs fa;
     for (int64_t c = 0; c < nck; ++c) {
-        CUDA_TRY(cudaMemcpyAsync(ckpt(c), seg(0), sbytes, cudaMemcpyDeviceToDevice, st));
-        fill_args(t, seg(0), fa);
+        CUDA_TRY(cudaMemcpyAsync(ckpt(c), work, sbytes, cudaMemcpyDeviceToDevice, st));
+        fill_args(t, work, fa);
         MTP_TRY(enqueue_layers(t, fa, c * K, std::min((c + 1) * K, nl), st));
     }
     // reverse sweep
@@ -652,19 +732,21 @@ int device_adjoint(Tents& t, const void* state0, const void* lamT, void* lam0, d
     AdjArgs aa;
     for (int64_t c = nck - 1; c >= 0; --c) {
         const int64_t l0 = c * K, l1 = std::min((c + 1) * K, nl);
+        const int64_t e0 = off[t.layer_ptr[l0]];
         MTP_TRY(set_front(t, l0, d.tau, st));
-        CUDA_TRY(cudaMemcpyAsync(seg(0), ckpt(c), sbytes, cudaMemcpyDeviceToDevice, st));
-        for (int64_t l = l0; l + 1 < l1; ++l) {
-            CUDA_TRY(cudaMemcpyAsync(seg(l - l0 + 1), seg(l - l0), sbytes, cudaMemcpyDeviceToDevice, st));
-            fill_args(t, seg(l - l0 + 1), fa);
-            MTP_TRY(enqueue_layers(t, fa, l, l + 1, st));
+        CUDA_TRY(cudaMemcpyAsync(work, ckpt(c), sbytes, cudaMemcpyDeviceToDevice, st));
+        fill_args(t, work, fa);
+        for (int64_t l = l0; l < l1; ++l) {
+            MTP_TRY(patch_tape(t, work, ptape, l, e0, seg_entries, true, st));
+            if (l + 1 < l1) MTP_TRY(enqueue_layers(t, fa, l, l + 1, st));
         }
         for (int64_t l = l1 - 1; l >= l0; --l) {
             const int64_t t0 = t.layer_ptr[l], n = t.layer_ptr[l + 1] - t0;
             if (n == 0) continue;
+            MTP_TRY(patch_tape(t, ybot, ptape, l, e0, seg_entries, false, st));
             fill_args(t, nullptr, aa.k);
             aa.k.tau = d.tau_rev;
-            aa.ybot = seg(l - l0);
+            aa.ybot = ybot;
             aa.lam = lam0;
             aa.geps = geps;
             aa.gmu = gmu;
@@ -710,8 +792,8 @@ int device_batch_evolve(Batch& b, void* const* states, void* stream) {
     static BatchEntry table[2][2];
     static bool init = false;
     if (!init) { batch_table(table); init = true; }
-    if (m0.precision == MTP_TF32 || m0.precision == MTP_TF32X3)
-        return set_error(MTP_EUNSUPPORTED, "batches run FP64 or FP32 SIMT meshes; tensor-core modes are per mesh");
+    if (m0.precision == MTP_TF32 || m0.precision == MTP_TF32X3 || m0.precision == MTP_FP32_SPLIT)
+        return set_error(MTP_EUNSUPPORTED, "batches run FP64 or FP32 SIMT meshes; tensor-core and split modes are per mesh");
     const BatchEntry& be = table[m0.precision == MTP_FP64 ? 0 : 1][m0.dim - 2];
     if (!b.dev) {
         b.dev = new DeviceBatch();

@@ -471,12 +471,11 @@ int mtp_mesh_create(int dim, int64_t n_verts, const double* vertices, int64_t n_
     if (n_verts < dim + 1 || n_elems < 1) return set_error(MTP_EINVAL, "mesh too small");
     if (n_verts > INT32_MAX || n_elems > INT32_MAX) return set_error(MTP_EINVAL, "mesh too large for int32 ids");
     if (opts->p < 1 || opts->p > kMaxDegree) return set_error(MTP_EUNSUPPORTED, "p must be in 1..5");
-    if (opts->precision >= MTP_TF32 && opts->p > 4)
-        return set_error(MTP_EUNSUPPORTED, "tensor-core precisions are built for p <= 4");
+    const bool tc = opts->precision == MTP_TF32 || opts->precision == MTP_TF32X3;
+    if (tc && opts->p > 4) return set_error(MTP_EUNSUPPORTED, "tensor-core precisions are built for p <= 4");
     if (opts->q < 0 || opts->m < 0 || opts->q > 8 || opts->m > 64) return set_error(MTP_EINVAL, "q must be in 0..8 and m in 0..64");
-    if (opts->precision < MTP_FP64 || opts->precision > MTP_TF32X3) return set_error(MTP_EINVAL, "unknown precision");
-    if (opts->precision >= MTP_TF32 && dim != 3)
-        return set_error(MTP_EUNSUPPORTED, "tensor-core precisions are built for 3D meshes");
+    if (opts->precision < MTP_FP64 || opts->precision > MTP_FP32_SPLIT) return set_error(MTP_EINVAL, "unknown precision");
+    if (tc && dim != 3) return set_error(MTP_EUNSUPPORTED, "tensor-core precisions are built for 3D meshes");
     if (opts->n_rhs < 0 || opts->n_rhs > 4096) return set_error(MTP_EINVAL, "n_rhs must be in 0..4096");
     if (opts->flags & ~(MTP_FLAG_LAYER_LAUNCHES | MTP_FLAG_TEST_STALL)) return set_error(MTP_EINVAL, "unknown flag bits");
     auto h = std::make_unique<mtp_mesh>();

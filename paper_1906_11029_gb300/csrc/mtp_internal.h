@@ -25,6 +25,12 @@ struct RefTables {
     int dim = 0, p = 0, nb = 0, nfb = 0;
     // S[j][l][a][b] = int_{T^} lambda_j psi_b d_l psi_a            (j <= dim, l < dim)
     std::vector<double> S;
+    // Factored volume tables, nbm = dim P_{p-1}: d_l psi_a lies in P_{p-1}, so with
+    // D[l][c][a] = int psi_c d_l psi_a and M[j][c][b] = int psi_c lambda_j psi_b (c < nbm),
+    // S[j][l][a][b] = sum_c D[l][c][a] M[j][c][b] exactly.
+    int nbm = 0;
+    std::vector<double> D;   // [l][c][a]
+    std::vector<double> M;   // [j][c][b]
     // Tr[f][c][a] = int_{F^} chi_c(s) psi_a(x_f(s)) ds              (facet f opposite vertex f)
     std::vector<double> Tr;
     // L[j][f][a][c] = int_{F^} lambda_j(x_f(s)) psi_a(x_f(s)) chi_c(s) ds

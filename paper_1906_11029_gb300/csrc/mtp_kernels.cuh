@@ -48,10 +48,12 @@ struct KArgs {
     const void* S;              // [j][l][a][NBP]  reference tables in the state precision,
     const void* Tr;             // [f][c][NBP]     rows padded with zeros (see pad4)
     const void* L;              // [j][f][a][NFBP]
-    // the same tables thread-major: with G = ceil(rows / AP) row groups (NAG or NCG, see
-    // Shape), entry (r, c) of one matrix at [c / W][r / G][r % G][c % W], W = elements per
-    // 16-byte vector; a thread owns rows g and g + G
-    const void* Sc;             // matrices (j, l), NB x NB
+    // thread-major tables of the SIMT kernels: with G = ceil(rows / AP) row groups (NWG,
+    // NAG or NCG, see Shape), entry (r, c) of one matrix at [c / W][r / G][r % G][c % W],
+    // W = elements per 16-byte vector; a thread owns rows g and g + G.  The volume term uses
+    // the factorisation S[j][l] = D[l]^T M[j] (d_l psi_a lies in P_{p-1}):
+    const void* Mc;             // matrices j, NBM x NB:  M[j][c][b] = int psi_c lambda_j psi_b
+    const void* Dc;             // matrices l, NB x NBM:  D[l]^T[a][c] = int psi_c d_l psi_a
     const void* Trc;            // matrices f, NFB x NB
     const void* Lc;             // matrices (j, f), NB x NFB
     // tensor-core modes: A-operand tables in m16n8k8 fragment order (32 lanes x 4 TF32 values
@@ -104,6 +106,19 @@ struct Shape {
     static constexpr bool VSPLIT = NAG <= NBLO;
     static constexpr int TDEG = degree_of(DIM - 1, NCG);
     static constexpr int TLO = dim_pk(DIM, TDEG - 1);
+    // Factored volume term: W = M_j U (rows c < NBM = dim P_{P-1}), then P_l = D_l^T W.
+    // D_l^T[a][c] = 0 unless deg c < deg a: a thread's first row (a < NAG, degree <= DA1) needs
+    // only c < CV1.  M_j[c][b] = 0 unless |deg b - deg c| <= 1: first W rows (c < NWG, degree
+    // <= DC1) need only b < BW1, second W rows (degree >= DC2) only b >= BW2.
+    static constexpr int NBM = dim_pk(DIM, P - 1);
+    static constexpr int NBMP = pad4(NBM);
+    static constexpr int NWG = (NBM + AP - 1) / AP;
+    static constexpr int DA1 = degree_of(DIM, NAG - 1);
+    static constexpr int CV1 = dim_pk(DIM, DA1 - 1);
+    static constexpr int DC1 = degree_of(DIM, NWG - 1);
+    static constexpr int BW1 = dim_pk(DIM, DC1 + 1);
+    static constexpr int DC2 = degree_of(DIM, NWG);
+    static constexpr int BW2 = dim_pk(DIM, DC2 - 2);
 };
 
 // CTAs per SM the register budget is shaped for (two 256-thread CTAs fit the FP32 3D
@@ -128,20 +143,40 @@ struct Vec<double> {
     static __device__ __forceinline__ void get(const T& v, double o[2]) { o[0] = v.x; o[1] = v.y; }
 };
 
+// MODE 0: SIMT contractions in the state precision; 1: TF32 tensor-core MMAs (FP32 state,
+// FP32 accumulate); 2: the same with a 3-term hi + lo split of both operands; 3: SIMT FP32
+// contractions with the Taylor sum carried as an FP32 pair hi + lo (two-sum) and an FP64
+// state between tents.
+template <int MODE>
+struct ModeTraits {
+    static constexpr bool simt = MODE == 0 || MODE == 3;
+    static constexpr bool split = MODE == 3;
+};
+template <typename Real, int MODE>
+using StateOf = typename std::conditional<ModeTraits<MODE>::split, double, Real>::type;
+
 // shared-memory carve-up, sizes from the mesh's largest patch
 template <typename Real, int DIM, int P>
 struct SmemLayout {
     using Sh = Shape<DIM, P>;
     static __host__ __device__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-    size_t off_Y, off_Ua, off_Ub, off_tr, off_Gi, off_gphi, off_gdel, off_mat, off_ac, off_gd, off_nrm,
-        off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, off_pair, off_own, bytes, state_bytes, tr_bytes;
-    __host__ __device__ explicit SmemLayout(int mp) {
+    size_t off_Y, off_Ylo, off_Ua, off_Ub, off_W, off_tr, off_Gi, off_gphi, off_gdel, off_mat, off_ac, off_gd,
+        off_nrm, off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, off_pair, off_own, bytes, state_bytes, tr_bytes;
+    bool split, factored, twobuf;
+    // mode (see ModeTraits): split carries the Taylor accumulator Y as an unevaluated pair
+    // hi + lo (one more patch-state buffer); the SIMT modes use the factored volume term (a W
+    // buffer) and update U in place, the tensor-core modes keep two U buffers (twobuf also
+    // asks for the second one, for the adjoint's reverse recursion)
+    __host__ __device__ explicit SmemLayout(int mp, int mode = 0, bool two = false)
+        : split(mode == 3), factored(mode == 0 || mode == 3), twobuf(two || !(mode == 0 || mode == 3)) {
         size_t o = 0;
         state_bytes = (size_t)mp * Sh::NF * Sh::NBP * sizeof(Real);
         tr_bytes = (size_t)mp * DIM * Sh::NF * Sh::NFBP * sizeof(Real);
         off_Y = o; o = align16(o + state_bytes);
+        off_Ylo = o; if (split) o = align16(o + state_bytes);
         off_Ua = o; o = align16(o + state_bytes);
-        off_Ub = o; o = align16(o + state_bytes);
+        off_Ub = o; if (twobuf) o = align16(o + state_bytes);
+        off_W = o; if (factored) o = align16(o + (size_t)mp * Sh::NF * Sh::NBMP * sizeof(Real));
         off_tr = o; o = align16(o + tr_bytes);
         off_Gi = o; o = align16(o + (size_t)mp * Sh::NF * Sh::GIS * sizeof(Real));
         off_gphi = o; o = align16(o + (size_t)mp * 3 * sizeof(double));
@@ -201,7 +236,7 @@ __device__ __forceinline__ int field6(int r) {   // index of field r inside (Ex,
 template <typename Real, int DIM, int P>
 struct TentCtx {
     using Sh = Shape<DIM, P>;
-    Real *sY, *sUa, *sUb, *sTr, *sGi;
+    Real *sY, *sYlo, *sUa, *sUb, *sW, *sTr, *sGi;   // sYlo / sUb / sW null when the layout has none
     double *sGphi, *sGdel, *sMat;
     Real *sAc, *sGd, *sNrm, *sLiftc, *sTrs, *sZ;
     int8_t *sJ, *sNslot, *sNfi, *sPair;   // sPair: [pair][2] element slots (second -1: single)
@@ -214,8 +249,10 @@ struct TentCtx {
 
     __device__ void carve(unsigned char* smem, const SmemLayout<Real, DIM, P>& lay) {
         sY = (Real*)(smem + lay.off_Y);
+        sYlo = lay.split ? (Real*)(smem + lay.off_Ylo) : nullptr;
         sUa = (Real*)(smem + lay.off_Ua);
-        sUb = (Real*)(smem + lay.off_Ub);
+        sUb = lay.twobuf ? (Real*)(smem + lay.off_Ub) : nullptr;
+        sW = lay.factored ? (Real*)(smem + lay.off_W) : nullptr;
         sTr = (Real*)(smem + lay.off_tr);
         sGi = (Real*)(smem + lay.off_Gi);
         sGphi = (double*)(smem + lay.off_gphi);
@@ -242,8 +279,8 @@ struct TentCtx {
 template <typename T>
 __device__ __forceinline__ T load_cg(const T* p) { return __ldcg(p); }
 
-template <typename Real, int DIM, int P, bool CG = false>
-__device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t tent, const Real* src) {
+template <typename Real, int DIM, int P, bool CG = false, typename SrcT = Real>
+__device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t tent, const SrcT* src) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NV = Sh::NV, NT = Sh::NT, NBP = Sh::NBP;
     constexpr int ESZ = NF * NBP, TSZ = DIM * NF * Sh::NFBP;
@@ -288,11 +325,20 @@ __device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t ten
     }
     for (int idx = tid; idx < ns * ESZ; idx += NT) {
         const int k = idx / ESZ, r = idx - k * ESZ, s = r / NBP, b = r - s * NBP;
-        const Real* sp = src + ((int64_t)a.patch_elem[c.pb + k] * NF + s) * NB + b;
-        c.sY[idx] = b < NB ? (CG ? load_cg(sp) : *sp) : Real(0);
+        const SrcT* sp = src + ((int64_t)a.patch_elem[c.pb + k] * NF + s) * NB + b;
+        const SrcT v = b < NB ? (CG ? load_cg(sp) : *sp) : SrcT(0);
+        if constexpr (std::is_same<SrcT, Real>::value) {
+            c.sY[idx] = v;
+        } else {   // FP64 state -> FP32 pair hi + lo (exact: |lo| <= ulp(hi) / 2)
+            const Real hi = (Real)v;
+            c.sY[idx] = hi;
+            c.sYlo[idx] = (Real)(v - (SrcT)hi);
+        }
         c.sUa[idx] = Real(0);
-        c.sUb[idx] = Real(0);
+        if (c.sUb) c.sUb[idx] = Real(0);
     }
+    if (c.sW)
+        for (int idx = tid; idx < ns * NF * Sh::NBMP; idx += NT) c.sW[idx] = Real(0);
     for (int idx = tid; idx < ns * TSZ; idx += NT) c.sTr[idx] = Real(0);
     __syncthreads();
     // neighbour's facet position (needs the neighbour's j) and impedance
@@ -391,9 +437,29 @@ __device__ void tent_ginv(TentCtx<Real, DIM, P>& c, const KArgs& a, int i) {
     }
 }
 
-// dst = G^-1 src per coefficient column (b < NB)
+// Error-free sum of two floats (Knuth's two-sum): hi + lo == a + b exactly, hi = fl(a + b).
+// The explicit round-to-nearest intrinsics keep the compiler from contracting or reordering.
+__device__ __forceinline__ void two_sum(float a, float b, float& hi, float& lo) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float aa = __fsub_rn(s, bb);
+    lo = __fadd_rn(__fsub_rn(a, aa), __fsub_rn(b, bb));
+    hi = s;
+}
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ void two_sum(double a, double b, double& hi, double& lo) {
+    const double s = __dadd_rn(a, b);
+    const double bb = __dsub_rn(s, a);
+    const double aa = __dsub_rn(s, bb);
+    lo = __dadd_rn(__dsub_rn(a, aa), __dsub_rn(b, bb));
+    hi = s;
+}
+
+// dst = G^-1 src per coefficient column (b < NB).  With a split accumulator the pair
+// (src, sYlo) is first renormalised so that src holds the correctly rounded sum.
 template <typename Real, int DIM, int P>
-__device__ void tent_apply_ginv(TentCtx<Real, DIM, P>& c, const Real* src, Real* dst) {
+__device__ void tent_apply_ginv(TentCtx<Real, DIM, P>& c, Real* src, Real* dst) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, ESZ = NF * Sh::NBP, NBP = Sh::NBP, GIS = Sh::GIS;
     for (int idx = threadIdx.x; idx < c.ns * NB; idx += blockDim.x) {
@@ -401,7 +467,16 @@ __device__ void tent_apply_ginv(TentCtx<Real, DIM, P>& c, const Real* src, Real*
         const Real* Gi = c.sGi + k * NF * GIS;
         Real y[NF];
 #pragma unroll
-        for (int s = 0; s < NF; ++s) y[s] = src[k * ESZ + s * NBP + b];
+        for (int s = 0; s < NF; ++s) {
+            const int i = k * ESZ + s * NBP + b;
+            if (c.sYlo) {
+                Real hi, lo;
+                two_sum(src[i], c.sYlo[i], hi, lo);
+                src[i] = hi;
+                c.sYlo[i] = lo;
+            }
+            y[s] = src[i];
+        }
 #pragma unroll
         for (int r = 0; r < NF; ++r) {
             Real acc = 0;
@@ -412,10 +487,89 @@ __device__ void tent_apply_ginv(TentCtx<Real, DIM, P>& c, const Real* src, Real*
     }
 }
 
+// W = M_j U for the factored volume term (rows c < NBM): one thread per (pair of elements
+// with the same local index j, or single element in FP64, two rows c and c + NWG); the rows'
+// zero blocks (|deg b - deg c| > 1) are skipped
+template <typename Real, int DIM, int P>
+__device__ __forceinline__ void tent_w_item(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real* Ucur, int w) {
+    using Sh = Shape<DIM, P>;
+    using VT = typename Vec<Real>::T;
+    constexpr int NF = Sh::NF, NBP = Sh::NBP, NBM = Sh::NBM, NBMP = Sh::NBMP, NWG = Sh::NWG;
+    constexpr int AP = Sh::AP, W = Vec<Real>::W, ESZ = NF * NBP, WSZ = NF * NBMP;
+    constexpr int EP = sizeof(Real) == 4 ? 2 : 1;
+    constexpr int WMAT = NBP * AP * NWG;
+    const int pi = w / NWG, g = w - pi * NWG;
+    const int k0 = EP == 2 ? c.sPair[2 * pi] : pi;
+    const int kk1 = EP == 2 ? c.sPair[2 * pi + 1] : -1;
+    const int kk[2] = {k0, kk1 >= 0 ? kk1 : k0};
+    const Real* Mg = (const Real*)a.Mc + (size_t)c.sJ[k0] * WMAT + g * W;
+    Real acc[EP][AP][NF];
+#pragma unroll
+    for (int e = 0; e < EP; ++e)
+#pragma unroll
+        for (int ci = 0; ci < AP; ++ci)
+#pragma unroll
+            for (int s = 0; s < NF; ++s) acc[e][ci][s] = 0;
+    // column block [b, b + W): rows R0 <= ci < R1
+    auto block = [&](int b, auto r0, auto r1) {
+        constexpr int R0 = decltype(r0)::value, R1 = decltype(r1)::value;
+        Real mv[AP][W];
+#pragma unroll
+        for (int ci = R0; ci < R1; ++ci) Vec<Real>::get(__ldg((const VT*)(Mg + b * AP * NWG + ci * NWG * W)), mv[ci]);
+#pragma unroll
+        for (int e = 0; e < EP; ++e) {
+            const Real* U = Ucur + kk[e] * ESZ;
+#pragma unroll
+            for (int s = 0; s < NF; ++s) {
+                Real u[W];
+                Vec<Real>::get(*(const VT*)(U + s * NBP + b), u);
+#pragma unroll
+                for (int v = 0; v < W; ++v)
+#pragma unroll
+                    for (int ci = R0; ci < R1; ++ci) acc[e][ci][s] += mv[ci][v] * u[v];
+            }
+        }
+    };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    constexpr int B2 = Sh::BW2 / W * W;                       // second rows vanish below
+    constexpr int B1 = (Sh::BW1 + W - 1) / W * W;             // first rows vanish from here
+    constexpr int B1c = B1 < NBP ? B1 : NBP;
+#pragma unroll 1
+    for (int b = 0; b < B2; b += W) block(b, I0{}, I1{});
+#pragma unroll 1
+    for (int b = B2; b < B1c; b += W) block(b, I0{}, I2{});
+#pragma unroll 1
+    for (int b = B1c; b < NBP; b += W) block(b, I1{}, I2{});
+#pragma unroll
+    for (int e = 0; e < EP; ++e) {
+        if (e == 1 && kk1 < 0) break;
+        Real* out = c.sW + kk[e] * WSZ;
+#pragma unroll
+        for (int ci = 0; ci < AP; ++ci) {
+            const int row = g + ci * NWG;
+            if (row < NBM) {
+#pragma unroll
+                for (int s = 0; s < NF; ++s) out[s * NBMP + row] = acc[e][ci][s];
+            }
+        }
+    }
+}
+
 // (b1) facet traces of U on the facets containing V: one thread per (element, two facet
-// modes), all DIM facets, so every 16-byte read of U feeds DIM x 2 x W FMAs
+// modes), all DIM facets, so every 16-byte read of U feeds DIM x 2 x W FMAs; with the
+// factored volume term (sW set) the same phase computes W = M_j U on the threads that the
+// last round of trace items leaves idle
 template <typename Real, int DIM, int P>
 __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real* Ucur, Real* tr) {
+    if (c.sW) {
+        constexpr int NT = Shape<DIM, P>::NT;
+        const int nitems = (sizeof(Real) == 4 ? *c.sNpair : c.ns) * Shape<DIM, P>::NWG;
+        const int busy = (c.ns * Shape<DIM, P>::NCG) % NT, idle = NT - busy;
+        if ((int)threadIdx.x >= busy)
+            for (int w = threadIdx.x - busy; w < nitems; w += idle) tent_w_item(c, a, Ucur, w);
+    }
     using Sh = Shape<DIM, P>;
     using VT = typename Vec<Real>::T;
     constexpr int NF = Sh::NF, NFB = Sh::NFB, NT = Sh::NT, NBP = Sh::NBP, NFBP = Sh::NFBP;
@@ -485,7 +639,7 @@ __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real
 template <typename Real, int DIM, int P>
 __device__ void tent_fluxes(TentCtx<Real, DIM, P>& c, Real* tr) {
     using Sh = Shape<DIM, P>;
-    constexpr int NF = Sh::NF, NFB = Sh::NFB, NT = Sh::NT, NFBP = Sh::NFBP, TSZ = DIM * NF * NFBP;
+    constexpr int NF = Sh::NF, NFB = Sh::NFB, NFBP = Sh::NFBP, TSZ = DIM * NF * NFBP;
     const int nown = *c.sNown;
     for (int idx = threadIdx.x; idx < nown * NFB; idx += blockDim.x) {
         const int oi = idx / NFB, cc = idx - oi * NFB;
@@ -521,7 +675,7 @@ __device__ void tent_fluxes(TentCtx<Real, DIM, P>& c, Real* tr) {
 // accumulation into sY, and U_{i,n} = G_i^-1 (Y_{i,n} - n M' U_{i,n-1}) into Unext (n < q).
 // One thread per (pair of elements with the same local index j, two basis functions): every
 // 16-byte read of the j-dependent tables S and L feeds both elements.
-template <typename Real, int DIM, int P>
+template <typename Real, int DIM, int P, bool SPLIT = false>
 __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, const Real* Ucur, Real* Unext,
                            const Real* tr) {
     using Sh = Shape<DIM, P>;
@@ -529,8 +683,8 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
     constexpr int NF = Sh::NF, NB = Sh::NB, NV = Sh::NV, NT = Sh::NT, NBP = Sh::NBP, NFBP = Sh::NFBP;
     constexpr int AP = Sh::AP, NAG = Sh::NAG, W = Vec<Real>::W, ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
     constexpr int EP = sizeof(Real) == 4 ? 2 : 1;   // elements per thread (FP64: register budget)
-    constexpr int SMAT = NBP * AP * NAG, LMAT = NFBP * AP * NAG;   // thread-major S and L matrices
-    const Real* S = (const Real*)a.Sc;
+    constexpr int NBMP = Sh::NBMP, WSZ = NF * NBMP;
+    constexpr int DMAT = NBMP * AP * NAG, LMAT = NFBP * AP * NAG;   // thread-major D^T and L matrices
     const Real* Lf = (const Real*)a.Lc;
     const Real cn = (Real)a.taylor[n];
     const Real nn = (Real)n;
@@ -545,6 +699,7 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
         const int j = c.sJ[k0];
         Real Yn[EP][AP][NF];
         {
+            const Real* Dg = (const Real*)a.Dc + ag * W;
             Real Pm[EP][AP][DIM][NF];
 #pragma unroll
             for (int e = 0; e < EP; ++e)
@@ -554,39 +709,40 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
                     for (int l = 0; l < DIM; ++l)
 #pragma unroll
                         for (int s = 0; s < NF; ++s) Pm[e][ai][l][s] = 0;
-            const Real* Sg = S + (size_t)j * DIM * SMAT + ag * W;
-            // column block [b, b + W) for both rows (A0 = 0) or the second row only (A0 = 1)
-            auto block = [&](int b, auto a0) {
+            // P_l = D_l^T W (factored volume, W = M_j U from phase b1); the D tables do not
+            // depend on j.  Column block [c, c + W) for both rows (A0 = 0) or the second only.
+            auto block = [&](int cb, auto a0) {
                 constexpr int A0 = decltype(a0)::value;
-                Real sv[AP][DIM][W];
-                const Real* Sb = Sg + b * AP * NAG;
+                Real dv[AP][DIM][W];
+                const Real* Db = Dg + cb * AP * NAG;
 #pragma unroll
                 for (int l = 0; l < DIM; ++l)
 #pragma unroll
                     for (int ai = A0; ai < AP; ++ai)
-                        Vec<Real>::get(__ldg((const VT*)(Sb + l * SMAT + ai * NAG * W)), sv[ai][l]);
+                        Vec<Real>::get(__ldg((const VT*)(Db + l * DMAT + ai * NAG * W)), dv[ai][l]);
 #pragma unroll
                 for (int e = 0; e < EP; ++e) {
-                    const Real* U = Ucur + kk[e] * ESZ;
+                    const Real* Wv = c.sW + kk[e] * WSZ;
 #pragma unroll
                     for (int s = 0; s < NF; ++s) {
                         Real u[W];
-                        Vec<Real>::get(*(const VT*)(U + s * NBP + b), u);
+                        Vec<Real>::get(*(const VT*)(Wv + s * NBMP + cb), u);
 #pragma unroll
                         for (int v = 0; v < W; ++v)
 #pragma unroll
                             for (int ai = A0; ai < AP; ++ai)
 #pragma unroll
-                                for (int l = 0; l < DIM; ++l) Pm[e][ai][l][s] += sv[ai][l][v] * u[v];
+                                for (int l = 0; l < DIM; ++l) Pm[e][ai][l][s] += dv[ai][l][v] * u[v];
                     }
                 }
             };
-            // first rows (degree < P) vanish from block BV on
-            constexpr int BV = Sh::VSPLIT ? (Sh::NBLO + W - 1) / W * W : NBP;
+            // first rows (degree <= DA1) need only columns c < CV1
+            constexpr int BV0 = (Sh::CV1 + W - 1) / W * W;
+            constexpr int BV = BV0 < NBMP ? BV0 : NBMP;
 #pragma unroll 1
-            for (int b = 0; b < BV; b += W) block(b, std::integral_constant<int, 0>{});
+            for (int cb = 0; cb < BV; cb += W) block(cb, std::integral_constant<int, 0>{});
 #pragma unroll 1
-            for (int b = BV; b < NBP; b += W) block(b, std::integral_constant<int, 1>{});
+            for (int cb = BV; cb < NBMP; cb += W) block(cb, std::integral_constant<int, 1>{});
 #pragma unroll
             for (int e = 0; e < EP; ++e) {
                 const Real* ac = c.sAc + kk[e] * DIM * 3;
@@ -673,8 +829,19 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
             for (int ai = 0; ai < AP; ++ai) {
                 if (ai == 1 && !two) break;
                 const int av = ag + ai * NAG;
+                if constexpr (SPLIT) {
 #pragma unroll
-                for (int s = 0; s < NF; ++s) c.sY[k * ESZ + s * NBP + av] += cn * Yn[e][ai][s];
+                    for (int s = 0; s < NF; ++s) {   // (hi, lo) += cn Yn: two-sum, error into lo
+                        const int i = k * ESZ + s * NBP + av;
+                        Real hi, err;
+                        two_sum(c.sY[i], mul_rn(cn, Yn[e][ai][s]), hi, err);
+                        c.sY[i] = hi;
+                        c.sYlo[i] += err;
+                    }
+                } else {
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) c.sY[k * ESZ + s * NBP + av] += cn * Yn[e][ai][s];
+                }
                 if (n < a.q) {
                     Real r6[NF];
                     if constexpr (DIM == 3) {
@@ -725,8 +892,6 @@ template <typename Real, int DIM, int P, int MODE>
 __device__ void tent_stage_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, const Real* Ucur, Real* Unext,
                               const Real* tr);
 
-// MODE 0: SIMT contractions in the state precision; 1: TF32 tensor-core MMAs (FP32 state,
-// FP32 accumulate); 2: the same with a 3-term hi + lo split of both operands.
 template <typename Real, int DIM, int P, int MODE = 0>
 __device__ void tent_sat(TentCtx<Real, DIM, P>& c, const KArgs& a, Real* tape) {
     constexpr int ESZ = Shape<DIM, P>::NF * Shape<DIM, P>::NBP;
@@ -735,21 +900,25 @@ __device__ void tent_sat(TentCtx<Real, DIM, P>& c, const KArgs& a, Real* tape) {
         tent_ginv(c, a, i);
         if (tape) tent_copy<Real, DIM, P>(c.ns, c.sY, tape + (size_t)i * slot);
         __syncthreads();
+        // SIMT modes update U in place (the factored stage reads only its own rows of U);
+        // the tensor-core stages read all of U while writing the next one
         Real* Ucur = c.sUa;
-        Real* Unext = c.sUb;
+        Real* Unext = ModeTraits<MODE>::simt ? c.sUa : c.sUb;
         tent_apply_ginv(c, c.sY, Ucur);
         __syncthreads();
         for (int n = 1; n <= a.q; ++n) {
             if (tape) tent_copy<Real, DIM, P>(c.ns, Ucur, tape + (size_t)(a.m + i * a.q + n - 1) * slot);
-            if constexpr (MODE == 0) tent_traces(c, a, Ucur, c.sTr);
+            if constexpr (ModeTraits<MODE>::simt) tent_traces(c, a, Ucur, c.sTr);
             else tent_traces_tc<Real, DIM, P, MODE>(c, a, Ucur, c.sTr);
             __syncthreads();
             tent_fluxes(c, c.sTr);
             __syncthreads();
-            if constexpr (MODE == 0) tent_stage(c, a, n, Ucur, Unext, c.sTr);
+            if constexpr (ModeTraits<MODE>::simt) tent_stage<Real, DIM, P, ModeTraits<MODE>::split>(c, a, n, Ucur, Unext, c.sTr);
             else tent_stage_tc<Real, DIM, P, MODE>(c, a, n, Ucur, Unext, c.sTr);
             __syncthreads();
-            Real* tmp = Ucur; Ucur = Unext; Unext = tmp;
+            if constexpr (!ModeTraits<MODE>::simt) {
+                Real* tmp = Ucur; Ucur = Unext; Unext = tmp;
+            }
         }
     }
 }
@@ -758,19 +927,21 @@ template <typename Real, int DIM, int P, int MODE = 0>
 __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::value) tent_layer_kernel(const KArgs a, int64_t t0) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NT = Sh::NT, NBP = Sh::NBP, ESZ = NF * NBP;
+    using StateT = StateOf<Real, MODE>;
     extern __shared__ __align__(16) unsigned char smem[];
-    const SmemLayout<Real, DIM, P> lay(a.max_patch);
+    const SmemLayout<Real, DIM, P> lay(a.max_patch, MODE);
     TentCtx<Real, DIM, P> c;
     c.carve(smem, lay);
     const int64_t tent = t0 + blockIdx.x;
-    Real* state = (Real*)a.state + (int64_t)blockIdx.y * a.rhs_stride;
+    StateT* state = (StateT*)a.state + (int64_t)blockIdx.y * a.rhs_stride;
     tent_setup(c, a, tent, state);
     tent_sat<Real, DIM, P, MODE>(c, a, (Real*)nullptr);
     // ---- (d) scatter the tent-top Y; advance the front at V ----
     bool bad = false;
     for (int idx = threadIdx.x; idx < c.ns * NF * NB; idx += NT) {
         const int k = idx / (NF * NB), r = idx - k * NF * NB, s = r / NB, b = r - s * NB;
-        const Real v = c.sY[k * ESZ + s * NBP + b];
+        StateT v = c.sY[k * ESZ + s * NBP + b];
+        if constexpr (ModeTraits<MODE>::split) v += (StateT)c.sYlo[k * ESZ + s * NBP + b];
         if (!isfinite((double)v)) bad = true;
         state[(int64_t)a.patch_elem[c.pb + k] * NF * NB + r] = v;
     }
@@ -816,8 +987,9 @@ __device__ __forceinline__ long long globaltimer() {
 template <typename Real, int DIM, int P, int MODE = 0>
 __device__ bool tent_dag_step(unsigned char* smem, const KArgs& a, const PArgs& pa, int64_t tent, int* s_abort) {
     using Sh = Shape<DIM, P>;
+    using StateT = StateOf<Real, MODE>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NT = Sh::NT, NBP = Sh::NBP, ESZ = NF * NBP;
-    const SmemLayout<Real, DIM, P> lay(a.max_patch);
+    const SmemLayout<Real, DIM, P> lay(a.max_patch, MODE);
     TentCtx<Real, DIM, P> c;
     c.carve(smem, lay);
     const int V = a.tent_v[tent];
@@ -847,13 +1019,14 @@ __device__ bool tent_dag_step(unsigned char* smem, const KArgs& a, const PArgs& 
     __syncthreads();
     if (*s_abort) return false;
     for (int r = 0; r < pa.n_rhs; ++r) {
-        Real* state = (Real*)a.state + (int64_t)r * a.rhs_stride;
+        StateT* state = (StateT*)a.state + (int64_t)r * a.rhs_stride;
         tent_setup<Real, DIM, P, true>(c, a, tent, state);
         tent_sat<Real, DIM, P, MODE>(c, a, (Real*)nullptr);
         bool bad = false;
         for (int idx = threadIdx.x; idx < c.ns * NF * NB; idx += NT) {
             const int k = idx / (NF * NB), rr = idx - k * NF * NB, s = rr / NB, b = rr - s * NB;
-            const Real v = c.sY[k * ESZ + s * NBP + b];
+            StateT v = c.sY[k * ESZ + s * NBP + b];
+            if constexpr (ModeTraits<MODE>::split) v += (StateT)c.sYlo[k * ESZ + s * NBP + b];
             if (!isfinite((double)v)) bad = true;
             state[(int64_t)a.patch_elem[c.pb + k] * NF * NB + rr] = v;
         }

@@ -25,7 +25,7 @@ inline bool smem_fits(size_t bytes) {
 // MTP_EUNSUPPORTED.
 template <typename Real, int DIM, int P, int MODE = 0>
 cudaError_t prepare_tent_kernel(int max_patch, size_t* smem_bytes) {
-    SmemLayout<Real, DIM, P> lay(max_patch);
+    SmemLayout<Real, DIM, P> lay(max_patch, MODE);
     *smem_bytes = lay.bytes;
     if (!smem_fits(lay.bytes)) return cudaErrorInvalidValue;
     return cudaFuncSetAttribute(tent_layer_kernel<Real, DIM, P, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -34,7 +34,7 @@ cudaError_t prepare_tent_kernel(int max_patch, size_t* smem_bytes) {
 
 template <typename Real, int DIM, int P, int MODE = 0>
 cudaError_t launch_tent_kernel(const KArgs& a, int64_t t0, int n_tents, int n_rhs, cudaStream_t st) {
-    SmemLayout<Real, DIM, P> lay(a.max_patch);
+    SmemLayout<Real, DIM, P> lay(a.max_patch, MODE);
     dim3 grid(n_tents, n_rhs);
     tent_layer_kernel<Real, DIM, P, MODE><<<grid, Shape<DIM, P>::NT, lay.bytes, st>>>(a, t0);
     return cudaGetLastError();
@@ -42,7 +42,7 @@ cudaError_t launch_tent_kernel(const KArgs& a, int64_t t0, int n_tents, int n_rh
 
 template <typename Real, int DIM, int P, int MODE = 0>
 cudaError_t prepare_persistent_kernel(int max_patch, int* blocks_per_sm) {
-    SmemLayout<Real, DIM, P> lay(max_patch);
+    SmemLayout<Real, DIM, P> lay(max_patch, MODE);
     if (!smem_fits(lay.bytes)) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(tent_persistent_kernel<Real, DIM, P, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.bytes);
@@ -53,7 +53,7 @@ cudaError_t prepare_persistent_kernel(int max_patch, int* blocks_per_sm) {
 
 template <typename Real, int DIM, int P, int MODE = 0>
 cudaError_t launch_persistent_kernel(const KArgs& a, const PArgs& pa, int grid, cudaStream_t st) {
-    SmemLayout<Real, DIM, P> lay(a.max_patch);
+    SmemLayout<Real, DIM, P> lay(a.max_patch, MODE);
     tent_persistent_kernel<Real, DIM, P, MODE><<<grid, Shape<DIM, P>::NT, lay.bytes, st>>>(a, pa);
     return cudaGetLastError();
 }
@@ -70,6 +70,8 @@ void kernel_table_f64(KernelEntry entries[2][5]);
 void kernel_table_f32(KernelEntry entries[2][5]);
 // tensor-core modes (3D only): entries[mode - 1][p - 1]
 void kernel_table_tc(KernelEntry entries[2][5]);
+// FP32 arithmetic with the split (hi + lo) Taylor accumulator and an FP64 state: entries[dim - 2][p - 1]
+void kernel_table_split(KernelEntry entries[2][5]);
 
 struct AdjArgs;
 using AdjLaunchFn = cudaError_t (*)(const AdjArgs&, int64_t t0, int n_tents, int n_rhs, cudaStream_t st);
@@ -93,28 +95,21 @@ struct BatchEntry {
 // entries[precision][dim - 2]
 void batch_table(BatchEntry entries[2][2]);
 
-#define MTP_KERNEL_TABLE(NAME, REAL)                                                   \
-    void NAME(KernelEntry e[2][5]) {                                                   \
-        e[0][0] = {launch_tent_kernel<REAL, 2, 1>, prepare_tent_kernel<REAL, 2, 1>, \
-                    launch_persistent_kernel<REAL, 2, 1>, prepare_persistent_kernel<REAL, 2, 1>};   \
-        e[0][1] = {launch_tent_kernel<REAL, 2, 2>, prepare_tent_kernel<REAL, 2, 2>, \
-                    launch_persistent_kernel<REAL, 2, 2>, prepare_persistent_kernel<REAL, 2, 2>};   \
-        e[0][2] = {launch_tent_kernel<REAL, 2, 3>, prepare_tent_kernel<REAL, 2, 3>, \
-                    launch_persistent_kernel<REAL, 2, 3>, prepare_persistent_kernel<REAL, 2, 3>};   \
-        e[0][3] = {launch_tent_kernel<REAL, 2, 4>, prepare_tent_kernel<REAL, 2, 4>, \
-                    launch_persistent_kernel<REAL, 2, 4>, prepare_persistent_kernel<REAL, 2, 4>};   \
-        e[0][4] = {launch_tent_kernel<REAL, 2, 5>, prepare_tent_kernel<REAL, 2, 5>, \
-                    launch_persistent_kernel<REAL, 2, 5>, prepare_persistent_kernel<REAL, 2, 5>};   \
-        e[1][0] = {launch_tent_kernel<REAL, 3, 1>, prepare_tent_kernel<REAL, 3, 1>, \
-                    launch_persistent_kernel<REAL, 3, 1>, prepare_persistent_kernel<REAL, 3, 1>};   \
-        e[1][1] = {launch_tent_kernel<REAL, 3, 2>, prepare_tent_kernel<REAL, 3, 2>, \
-                    launch_persistent_kernel<REAL, 3, 2>, prepare_persistent_kernel<REAL, 3, 2>};   \
-        e[1][2] = {launch_tent_kernel<REAL, 3, 3>, prepare_tent_kernel<REAL, 3, 3>, \
-                    launch_persistent_kernel<REAL, 3, 3>, prepare_persistent_kernel<REAL, 3, 3>};   \
-        e[1][3] = {launch_tent_kernel<REAL, 3, 4>, prepare_tent_kernel<REAL, 3, 4>, \
-                    launch_persistent_kernel<REAL, 3, 4>, prepare_persistent_kernel<REAL, 3, 4>};   \
-        e[1][4] = {launch_tent_kernel<REAL, 3, 5>, prepare_tent_kernel<REAL, 3, 5>, \
-                    launch_persistent_kernel<REAL, 3, 5>, prepare_persistent_kernel<REAL, 3, 5>};   \
+#define MTP_KERNEL_ENTRY(REAL, D, P, MODE)                                                      \
+    KernelEntry{launch_tent_kernel<REAL, D, P, MODE>, prepare_tent_kernel<REAL, D, P, MODE>,     \
+                launch_persistent_kernel<REAL, D, P, MODE>, prepare_persistent_kernel<REAL, D, P, MODE>}
+#define MTP_KERNEL_TABLE(NAME, REAL, MODE)                                                      \
+    void NAME(KernelEntry e[2][5]) {                                                            \
+        e[0][0] = MTP_KERNEL_ENTRY(REAL, 2, 1, MODE);                              \
+        e[0][1] = MTP_KERNEL_ENTRY(REAL, 2, 2, MODE);                              \
+        e[0][2] = MTP_KERNEL_ENTRY(REAL, 2, 3, MODE);                              \
+        e[0][3] = MTP_KERNEL_ENTRY(REAL, 2, 4, MODE);                              \
+        e[0][4] = MTP_KERNEL_ENTRY(REAL, 2, 5, MODE);                              \
+        e[1][0] = MTP_KERNEL_ENTRY(REAL, 3, 1, MODE);                              \
+        e[1][1] = MTP_KERNEL_ENTRY(REAL, 3, 2, MODE);                              \
+        e[1][2] = MTP_KERNEL_ENTRY(REAL, 3, 3, MODE);                              \
+        e[1][3] = MTP_KERNEL_ENTRY(REAL, 3, 4, MODE);                              \
+        e[1][4] = MTP_KERNEL_ENTRY(REAL, 3, 5, MODE);                              \
     }
 
 }  // namespace mtp

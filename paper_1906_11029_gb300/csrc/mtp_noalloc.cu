@@ -87,8 +87,7 @@ extern "C" int mtp_energy_noalloc(const void* state_dev, const double* eps_dev, 
     if (dim != 2 && dim != 3) return set_error(MTP_EINVAL, "dim must be 2 or 3");
     if (p < 1 || p > kMaxDegree) return set_error(MTP_EINVAL, "p must be in 1..5");
     if (n_elems < 1) return set_error(MTP_EINVAL, "n_elems must be positive");
-    if (precision != MTP_FP64 && precision != MTP_FP32 && precision != MTP_TF32 && precision != MTP_TF32X3)
-        return set_error(MTP_EINVAL, "unknown precision");
+    if (precision < MTP_FP64 || precision > MTP_FP32_SPLIT) return set_error(MTP_EINVAL, "unknown precision");
     if (n_rhs < 1 || n_rhs > kNoAllocMaxRhs)
         return set_error(MTP_EINVAL, "n_rhs must be in 1.." + std::to_string(kNoAllocMaxRhs) +
                                          " (size of the static scratch of mtp_energy_noalloc)");
@@ -98,7 +97,7 @@ extern "C" int mtp_energy_noalloc(const void* state_dev, const double* eps_dev, 
     if (rc != MTP_OK) return rc;
     const int nf = n_fields(dim), nb = n_basis(dim, p);
     dim3 grid(kNoAllocBlocks, n_rhs);
-    if (precision == MTP_FP64)
+    if (precision == MTP_FP64 || precision == MTP_FP32_SPLIT)   // double states
         energy_partial_noalloc_kernel<double><<<grid, kNoAllocThreads, 0, st>>>(
             (const double*)state_dev, eps_dev, mu_dev, n_elems, nf, nb, scratch);
     else   // MTP_FP32, MTP_TF32, MTP_TF32X3: float states

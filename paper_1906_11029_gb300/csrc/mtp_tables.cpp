@@ -268,6 +268,18 @@ RefTables build_ref_tables(int d, int p) {
                 for (int a = 0; a < nb; ++a)
                     t.S[(((size_t)j * d + l) * nb + a) * nb + b] = (double)integrate(mul(lb, dpsi[l][a]), d);
         }
+    // factored volume tables (c < nbm = dim P_{p-1}; the basis is ordered by degree)
+    const int nbm = t.nbm = (int)std::count_if(dpsi_deg.begin(), dpsi_deg.end(), [&](int g) { return g < p; });
+    t.D.assign((size_t)d * nbm * nb, 0.0);
+    t.M.assign((size_t)(d + 1) * nbm * nb, 0.0);
+    for (int l = 0; l < d; ++l)
+        for (int c = 0; c < nbm; ++c)
+            for (int a = 0; a < nb; ++a) t.D[((size_t)l * nbm + c) * nb + a] = (double)integrate(mul(psi[c], dpsi[l][a]), d);
+    for (int j = 0; j <= d; ++j)
+        for (int c = 0; c < nbm; ++c) {
+            Poly lc = mul(lam[j], psi[c]);
+            for (int b = 0; b < nb; ++b) t.M[((size_t)j * nbm + c) * nb + b] = (double)integrate(mul(lc, psi[b]), d);
+        }
     // facets
     t.Tr.assign((size_t)(d + 1) * nfb * nb, 0.0);
     t.L.assign((size_t)(d + 1) * (d + 1) * nb * nfb, 0.0);
@@ -319,6 +331,30 @@ RefTables build_ref_tables(int d, int p) {
         for (int a = 0; a < nb; ++a)
             for (int c = 0; c < nfb; ++c)
                 if (dchi_deg[c] > dpsi_deg[a] + 1) zero(t.L[(jf * nb + a) * nfb + c], lmax);
+    // factored tables: D[l][c][a] = 0 unless deg c < deg a (d_l psi_a has degree deg a - 1);
+    // M[j][c][b] = 0 unless |deg b - deg c| <= 1 (lambda_j psi_c has degree deg c + 1)
+    double dmax = 0, mmax = 0;
+    for (double v : t.D) dmax = std::fmax(dmax, std::fabs(v));
+    for (double v : t.M) mmax = std::fmax(mmax, std::fabs(v));
+    for (int l = 0; l < d; ++l)
+        for (int c = 0; c < nbm; ++c)
+            for (int a = 0; a < nb; ++a)
+                if (dpsi_deg[c] >= dpsi_deg[a]) zero(t.D[((size_t)l * nbm + c) * nb + a], dmax);
+    for (int j = 0; j <= d; ++j)
+        for (int c = 0; c < nbm; ++c)
+            for (int b = 0; b < nb; ++b)
+                if (std::abs(dpsi_deg[b] - dpsi_deg[c]) > 1) zero(t.M[((size_t)j * nbm + c) * nb + b], mmax);
+    // the factorisation reproduces S (an independent product of exact integrals)
+    for (int j = 0; j <= d; ++j)
+        for (int l = 0; l < d; ++l)
+            for (int a = 0; a < nb; ++a)
+                for (int b = 0; b < nb; ++b) {
+                    ld acc = 0;
+                    for (int c = 0; c < nbm; ++c)
+                        acc += (ld)t.D[((size_t)l * nbm + c) * nb + a] * (ld)t.M[((size_t)j * nbm + c) * nb + b];
+                    if (!(std::fabs((double)acc - t.S[(((size_t)j * d + l) * nb + a) * nb + b]) <= 1e-12 * smax))
+                        throw std::runtime_error("reference tables: factored volume tables do not reproduce S");
+                }
     // lattice Vandermonde (point order: i_d outermost, i_1 innermost)
     std::vector<ld> V((size_t)nb * nb);
     int k = 0;

@@ -112,6 +112,16 @@ def test_tensor_core_precision_is_3d_only():
     assert ex.value.code == mtp.MTP_EUNSUPPORTED
 
 
+def test_split_precision_accepted_any_dim_and_state_is_double():
+    for dim, (v, e) in ((2, S.square_mesh(2)), (3, S.cube_mesh(1))):
+        m = mtp.Mesh(dim, v, e, np.ones(len(e)), np.ones(len(e)), p=5, precision=mtp.MTP_FP32_SPLIT)
+        import torch
+        assert m.torch_dtype() == torch.float64
+    with pytest.raises(mtp.MtpError) as ex:
+        mtp.Mesh(2, v, e, np.ones(len(e)), np.ones(len(e)), p=2, precision=mtp.MTP_FP32_SPLIT + 1)
+    assert ex.value.code == mtp.MTP_EINVAL
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_reference_tables_build_for_every_degree(dim):
     """Mesh creation builds the reference tables; it fails if either basis is not in

@@ -13,14 +13,15 @@ import mtp_synth as S
 import paper_1906_11029_gb300 as mtp
 
 pytestmark = pytest.mark.gpu
-TOL = {mtp.MTP_FP64: 1e-11, mtp.MTP_FP32: 1e-5, mtp.MTP_TF32: 1e-5, mtp.MTP_TF32X3: 1e-5}
+TOL = {mtp.MTP_FP64: 1e-11, mtp.MTP_FP32: 1e-5, mtp.MTP_TF32: 1e-5, mtp.MTP_TF32X3: 1e-5, mtp.MTP_FP32_SPLIT: 1e-11}
 CASES = [(2, mtp.MTP_FP64), (2, mtp.MTP_FP32), (3, mtp.MTP_FP64), (3, mtp.MTP_FP32), (3, mtp.MTP_TF32),
-         (3, mtp.MTP_TF32X3)]
+         (3, mtp.MTP_TF32X3), (3, mtp.MTP_FP32_SPLIT)]
 
 
 @pytest.mark.parametrize("dim,precision", CASES)
 def test_energy_noalloc_matches_energy(dim, precision):
-    """Tensor-core meshes keep float states like FP32 ones, so they are reduced the same way."""
+    """Tensor-core meshes keep float states like FP32 ones and split meshes double states like
+    FP64 ones, so each is reduced the same way as the corresponding plain mesh."""
     w = S.te_square(5, 3, 0.1) if dim == 2 else S.graded_sphere(n=3, p=3, T=0.05)
     n_rhs = 3
     m = mtp.Mesh(dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=precision, n_rhs=n_rhs)
