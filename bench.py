@@ -357,7 +357,7 @@ def run_equal_error(args):
     import paper_1906_11029_gb300 as mtp
     w4 = make_workload(args.workload)
     out, times, dofs = {}, {}, {}
-    runs = [(5, mtp.MTP_FP32), (4, mtp.MTP_FP32), (4, mtp.MTP_TF32), (4, mtp.MTP_TF32X3)]
+    runs = [(5, mtp.MTP_FP32), (4, mtp.MTP_FP32), (4, mtp.MTP_TF32), (4, mtp.MTP_TF32X3), (4, mtp.MTP_FP32_SPLIT)]
     if args.equal_error_fp64:
         runs.append((4, mtp.MTP_FP64))
     for p, prec in runs:
@@ -379,22 +379,24 @@ def run_equal_error(args):
     up = lambda u4: np.einsum("kl,elf->ekf", I, u4)
     ref = out[(4, mtp.MTP_FP32)]
     rel = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))
-    names = {mtp.MTP_FP32: "fp32", mtp.MTP_TF32: "tf32", mtp.MTP_TF32X3: "tf32x3", mtp.MTP_FP64: "fp64"}
+    names = {mtp.MTP_FP32: "fp32", mtp.MTP_TF32: "tf32", mtp.MTP_TF32X3: "tf32x3", mtp.MTP_FP64: "fp64",
+             mtp.MTP_FP32_SPLIT: "fp32split"}
     res = {"workload": w4.name, "e_disc_p4_vs_p5": rel(up(ref), u5),
            "ms": {f"p{p}_{names[q]}": v for (p, q), v in times.items()}}
-    for q in (mtp.MTP_TF32, mtp.MTP_TF32X3):
+    for q in (mtp.MTP_TF32, mtp.MTP_TF32X3, mtp.MTP_FP32_SPLIT):
         res[f"{names[q]}_vs_fp32"] = rel(out[(4, q)], ref)
     if (4, mtp.MTP_FP64) in out:
         # the whole evolve to T in FP64: each FP32-state mode against it, and against e_disc
         u64 = out[(4, mtp.MTP_FP64)]
         res["e_disc_fp64_p4_vs_p5"] = rel(up(u64), u5)
-        for q in (mtp.MTP_FP32, mtp.MTP_TF32, mtp.MTP_TF32X3):
+        for q in (mtp.MTP_FP32, mtp.MTP_TF32, mtp.MTP_TF32X3, mtp.MTP_FP32_SPLIT):
             d = rel(out[(4, q)], u64)
             res[f"{names[q]}_vs_fp64_full_T"] = d
             res[f"{names[q]}_vs_fp64_over_e_disc"] = d / res["e_disc_fp64_p4_vs_p5"]
         rate = lambda k: dofs[k] / (times[k] / 1e3)
         res["fp64_value"] = rate((4, mtp.MTP_FP64))
         res["fp32_value"] = rate((4, mtp.MTP_FP32))
+        res["fp32split_value"] = rate((4, mtp.MTP_FP32_SPLIT))
         res["fp32_speedup_vs_fp64_full_T"] = times[(4, mtp.MTP_FP64)] / times[(4, mtp.MTP_FP32)]
     print(json.dumps(res))
 
@@ -426,6 +428,35 @@ def adjoint_timing(reps=3):
     f, g = min(fw[1:]), min(ad[1:])
     return {"workload": w.name, "layers": t.info["n_layers"], "tents": t.info["n_tents"], "forward_ms": f,
             "adjoint_ms": g, "adjoint_over_forward": g / f}
+
+
+def run_rk4_study(args):
+    """2D TE cavity (Sec. 5.1 convergence study, FP64): lattice l2 errors of SAT and of the
+    Y-substituted classical RK4 tent stepper (MTP_FLAG_SUBSTITUTED_RK4) on the same tents, and
+    their distance (the RK4 time-stepping error), for p = 1..4 and n = 4..64."""
+    import torch
+    import mtp_synth as S
+    import paper_1906_11029_gb300 as mtp
+    rows = []
+    for p in (1, 2, 3, 4):
+        for n in (4, 8, 16, 32, 64):
+            w = S.te_square(n, p, 0.25)
+            pts = S.lattice_points(w.verts, w.elems, p)
+            E0, H0 = w.exact(pts, 0.0)
+            ET, HT = w.exact(pts, w.T)
+            v0 = np.ascontiguousarray(np.concatenate([E0, H0], -1)[..., [0, 1, 5]])
+            ex = np.concatenate([ET, HT], -1)[..., [0, 1, 5]]
+            out = {}
+            for flags in (0, mtp.MTP_FLAG_SUBSTITUTED_RK4):
+                m = mtp.Mesh(2, w.verts, w.elems, w.eps, w.mu, p=p, precision=mtp.MTP_FP64, flags=flags)
+                t = m.pitch(w.T, w.causality)
+                st = m.state_from_lattice(torch.tensor(v0[None], device="cuda"))
+                t.evolve(st)
+                out[flags] = m.state_to_lattice(st).cpu().numpy()[0]
+            rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+            rows.append({"p": p, "n": n, "sat": rel(out[0], ex), "rk4": rel(out[mtp.MTP_FLAG_SUBSTITUTED_RK4], ex),
+                         "rk4_minus_sat": rel(out[mtp.MTP_FLAG_SUBSTITUTED_RK4], out[0])})
+            print(json.dumps(rows[-1]), flush=True)
 
 
 def max_over_ranks(ms, dist, device):
@@ -467,6 +498,8 @@ def run_mtp(args):
     mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=prec, flags=flags)
     t1 = time.perf_counter()
     tents = mesh.pitch(w.T, w.causality)
+    if args.variant:
+        tents.set_variant(args.variant)
     t2 = time.perf_counter()
     tents_dev = mesh.pitch(w.T, w.causality, device=True)    # same tent list, rounds on the GPU
     t3 = time.perf_counter()
@@ -527,7 +560,7 @@ def run_mtp(args):
     traffic = None if tpl is None else tpl * tents.info["n_tents"] / launches_per_step
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": f"{kname}<{args.precision},3,{w.p}>", "peak_source": src,
+                "kernel": f"{kname}<{args.precision},3,{w.p}>", "kernel_variant": args.variant, "peak_source": src,
                 "probe_tflops": probe, "fp32_unit_count_peak": unit_peak, "sms": n_sms,
                 "frac_of_unit_count_peak": achieved / unit_peak if prec == mtp.MTP_FP32 else None,
                 "kernel_sources": kernel_source_hash()}
@@ -625,6 +658,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--fp64-window", type=float, default=0.02)
     ap.add_argument("--layer-launches", action="store_true", help="one launch per layer instead of the DAG walk")
+    ap.add_argument("--variant", type=int, default=0, help="tent kernel shape variant (mtp_tents_set_variant)")
     ap.add_argument("--cpu-tents", type=int, default=80, help="oracle baseline: tents (per process)")
     ap.add_argument("--cpu-rounds", type=int, default=80)
     ap.add_argument("--ref-tents", type=int, default=20, help="reference arm: tents per host core per step")
@@ -638,6 +672,7 @@ def main():
     ap.add_argument("--equal-error", action="store_true", help="p=4 precision modes against p=5")
     ap.add_argument("--equal-error-fp64", action="store_true",
                     help="with --equal-error: also one full FP64 p=4 evolve (about 10 min on the graded workload)")
+    ap.add_argument("--rk4-study", action="store_true", help="SAT vs substituted RK4 convergence table (2D, FP64)")
     ap.add_argument("--seed", type=int, default=7)
     args = ap.parse_args()
     if args.cpu_worker:
@@ -652,6 +687,8 @@ def main():
         return run_many(args)
     if args.equal_error:
         return run_equal_error(args)
+    if args.rk4_study:
+        return run_rk4_study(args)
     return run_mtp(args)
 
 

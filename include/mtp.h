@@ -55,6 +55,10 @@ extern "C" {
 #define MTP_FLAG_TEST_STALL     2   /* failure injection for tests: the persistent evolve never
                                        publishes the completion of its first tent and waits at most
                                        0.2 s, so it must return MTP_ETIMEOUT */
+#define MTP_FLAG_SUBSTITUTED_RK4 4  /* negative control for convergence studies (Sec. 3, after eq.
+                                       equ_ode; Sec. 5.1, Fig. 3 right): advance each tent with m
+                                       classical RK4 steps on d/dt Y = A M(t)^-1 Y instead of SAT;
+                                       MTP_FP64 only; not for batches or the adjoint */
 
 /* precision of the state and of the operator arithmetic */
 #define MTP_FP64   0   /* FP64 state and arithmetic */
@@ -163,6 +167,16 @@ int mtp_evolve(mtp_tents_t tents, void* state_dev, double T, void* stream);
  * many CTAs per SM as fit, 1 the DAG walk with one CTA per SM, 2 one launch per layer (CUDA
  * graph).  MTP_FLAG_LAYER_LAUNCHES on the mesh forces 2. */
 int mtp_tents_set_launch(mtp_tents_t tents, int launch);
+
+/* Kernel shape variant of this tents handle (MTP_FP32 SAT meshes): 0 (default) each stage item
+ * of the tent kernel covers a pair of patch elements with the same local index of the tent
+ * vertex, which share every reference-table read; 1 each item covers one element: twice the
+ * items at half the work each, so a tent finishes sooner when the layers hold fewer tents than
+ * the GPU has CTA slots (e.g. small meshes), at a lower throughput when they hold more;
+ * 2 each item covers one element and one basis function (or facet mode), with 512 threads per
+ * CTA in 3D: the shortest tents for such latency-bound layers.  Results are identical up to
+ * rounding order.  MTP_EUNSUPPORTED for variants 1 and 2 on other meshes. */
+int mtp_tents_set_variant(mtp_tents_t tents, int variant);
 
 /* Autotuner: times the three launch configurations on layers [layer_begin, layer_end) of
  * scratch_state_dev (overwritten with evolved values) and keeps the fastest for this handle;

@@ -22,14 +22,14 @@ LIB_PATH = os.path.join(HERE, "_lib", "libmtp.so")
 MTP_OK, MTP_EINVAL, MTP_EMESH, MTP_ECAUSAL = 0, -1, -2, -3
 MTP_ENOMEM, MTP_ECUDA, MTP_ETIMEOUT, MTP_ENUMERIC, MTP_EUNSUPPORTED = -4, -5, -6, -7, -8
 MTP_FP64, MTP_FP32, MTP_TF32, MTP_TF32X3, MTP_FP32_SPLIT = 0, 1, 2, 3, 4
-MTP_FLAG_LAYER_LAUNCHES, MTP_FLAG_TEST_STALL = 1, 2
+MTP_FLAG_LAYER_LAUNCHES, MTP_FLAG_TEST_STALL, MTP_FLAG_SUBSTITUTED_RK4 = 1, 2, 4
 _CODES = {0: "MTP_OK", -1: "MTP_EINVAL", -2: "MTP_EMESH", -3: "MTP_ECAUSAL", -4: "MTP_ENOMEM",
           -5: "MTP_ECUDA", -6: "MTP_ETIMEOUT", -7: "MTP_ENUMERIC", -8: "MTP_EUNSUPPORTED"}
 
 ABI_SYMBOLS = ["mtp_mesh_create", "mtp_mesh_destroy", "mtp_mesh_info", "mtp_pitch_tents", "mtp_pitch_tents_device",
                "mtp_tents_destroy", "mtp_tents_info", "mtp_tents_get", "mtp_state_from_lattice",
                "mtp_state_to_lattice", "mtp_evolve", "mtp_evolve_layers", "mtp_evolve_host",
-               "mtp_tents_set_launch", "mtp_tents_autotune", "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_info", "mtp_batch_evolve",
+               "mtp_tents_set_launch", "mtp_tents_set_variant", "mtp_tents_autotune", "mtp_batch_create", "mtp_batch_destroy", "mtp_batch_info", "mtp_batch_evolve",
                "mtp_adjoint", "mtp_energy", "mtp_energy_noalloc", "mtp_probe_rates", "mtp_last_error"]
 
 
@@ -65,6 +65,7 @@ def _load():
         "mtp_evolve_layers": (C.c_int, [P, P, I64, I64, P]),
         "mtp_evolve_host": (C.c_int, [P, P, P, D, P]),
         "mtp_tents_set_launch": (C.c_int, [P, C.c_int]),
+        "mtp_tents_set_variant": (C.c_int, [P, C.c_int]),
         "mtp_tents_autotune": (C.c_int, [P, P, I64, I64, P, P, P]),
         "mtp_batch_create": (C.c_int, [I64, P, C.POINTER(P)]),
         "mtp_batch_destroy": (None, [P]),
@@ -197,6 +198,10 @@ def mtp_evolve_host(tents, state_in, state_out, T, stream=None):
 
 def mtp_tents_set_launch(h, launch):
     _check(_lib.mtp_tents_set_launch(h, launch))
+
+
+def mtp_tents_set_variant(h, variant):
+    _check(_lib.mtp_tents_set_variant(h, variant))
 
 
 def mtp_tents_autotune(h, scratch_state, layer_begin, layer_end, stream=None):
@@ -364,6 +369,9 @@ class Tents:
 
     def set_launch(self, launch):
         mtp_tents_set_launch(self.h, launch)
+
+    def set_variant(self, variant):
+        mtp_tents_set_variant(self.h, variant)
 
     def autotune(self, scratch_state, layer_begin, layer_end, stream=None):
         return mtp_tents_autotune(self.h, scratch_state, layer_begin, layer_end, stream)

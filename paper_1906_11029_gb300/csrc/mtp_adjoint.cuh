@@ -94,7 +94,8 @@ template <typename Real, int DIM, int P>
 __global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_adjoint_kernel(const AdjArgs A, int64_t t0) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NFB = Sh::NFB, NV = Sh::NV, NT = Sh::NT;
-    constexpr int NBP = Sh::NBP, NFBP = Sh::NFBP, ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
+    constexpr int NBP = Sh::NBP, NFBP = Sh::NFBP, ESZ = NF * NBP, TSZ = Strides<Real, DIM, P>::TSZ;
+    constexpr int FSZ = Strides<Real, DIM, P>::FSZ;
     const KArgs& a = A.k;
     extern __shared__ __align__(16) unsigned char smem[];
     const AdjLayout<Real, DIM, P> lay(a.max_patch);
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_adjoint_kernel(const A
                     const Real l = __ldg(Lr + (size_t)av * NFBP);
                     for (int s = 0; s < NF; ++s) acc[s] += l * sLY[k * ESZ + s * NBP + av];
                 }
-                for (int s = 0; s < NF; ++s) sGh[k * TSZ + fi * NF * NFBP + s * NFBP + cc] = -acc[s];
+                for (int s = 0; s < NF; ++s) sGh[k * TSZ + fi * FSZ + s * NFBP + cc] = -acc[s];
             }
             __syncthreads();
             // flux transpose (owner of each facet) and dJ/dZ
@@ -188,8 +189,8 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_adjoint_kernel(const A
                 const int s2 = c.sNslot[k * DIM + fi];
                 if (s2 >= 0 && s2 < k) continue;
                 const int fi2 = s2 >= 0 ? c.sNfi[k * DIM + fi] : 0;
-                Real* gmine = sGh + k * TSZ + fi * NF * NFBP + cc;
-                Real* gother = s2 >= 0 ? sGh + s2 * TSZ + fi2 * NF * NFBP + cc : nullptr;
+                Real* gmine = sGh + k * TSZ + fi * FSZ + cc;
+                Real* gother = s2 >= 0 ? sGh + s2 * TSZ + fi2 * FSZ + cc : nullptr;
                 const Real lc = c.sLiftc[k * DIM + fi];
                 Real Fb[6] = {0, 0, 0, 0, 0, 0};
                 for (int s = 0; s < NF; ++s) {
@@ -203,12 +204,12 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_adjoint_kernel(const A
                 Real ubm[6], ubp[6];
                 upwind6_adjoint<Real>(Fb, nrm, Zm, Zp, ubm, ubp);
                 // forward traces for the impedance derivatives
-                const Real* tm = sTrU + k * TSZ + fi * NF * NFBP + cc;
+                const Real* tm = sTrU + k * TSZ + fi * FSZ + cc;
                 Dual<Real> um[6], up[6], dn[3], F[6];
                 for (int s = 0; s < 6; ++s) um[s] = up[s] = Dual<Real>(Real(0));
                 for (int s = 0; s < NF; ++s) um[field6<DIM>(s)] = Dual<Real>(tm[s * NFBP]);
                 if (gother) {
-                    const Real* tp = sTrU + s2 * TSZ + fi2 * NF * NFBP + cc;
+                    const Real* tp = sTrU + s2 * TSZ + fi2 * FSZ + cc;
                     for (int s = 0; s < NF; ++s) up[field6<DIM>(s)] = Dual<Real>(tp[s * NFBP]);
                 } else {
                     for (int s = 0; s < 6; ++s) up[s] = s < 3 ? -um[s] : um[s];
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT) tent_adjoint_kernel(const A
                 const Real sc = c.sTrs[k];
                 for (int fi = 0; fi < DIM; ++fi) {
                     const int f = fi + (fi >= j ? 1 : 0);
-                    const Real* gh = sGh + k * TSZ + fi * NF * NFBP;
+                    const Real* gh = sGh + k * TSZ + fi * FSZ;
                     for (int cc = 0; cc < NFB; ++cc) {
                         const Real t = __ldg(Tr + ((size_t)f * NFB + cc) * NBP + b) * sc;
                         for (int s = 0; s < NF; ++s) u[s] += t * gh[s * NFBP + cc];

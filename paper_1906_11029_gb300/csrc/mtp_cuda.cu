@@ -35,6 +35,10 @@ struct DeviceMesh {
     void* Dc = nullptr;
     void* Trc = nullptr;
     void* Lc = nullptr;
+    void* Mc1 = nullptr;          // the same four tables with one row per thread (shape variant 2)
+    void* Dc1 = nullptr;
+    void* Trc1 = nullptr;
+    void* Lc1 = nullptr;
     double* V = nullptr;
     double* Vinv = nullptr;
     float* Sf = nullptr;          // tensor-core fragment tables (TF32 modes)
@@ -189,6 +193,12 @@ int device_mesh_upload(Mesh& m) {
         MTP_TRY(upload_real(m, &d.Dc, thread_major(Dt, m.dim, m.nb, nbm, w, ap)));
         MTP_TRY(upload_real(m, &d.Trc, thread_major(m.ref.Tr, nv, m.nfb, m.nb, w, ap)));
         MTP_TRY(upload_real(m, &d.Lc, thread_major(m.ref.L, nv * nv, m.nb, m.nfb, w, ap)));
+        if (m.precision == MTP_FP32) {
+            MTP_TRY(upload_real(m, &d.Mc1, thread_major(m.ref.M, nv, nbm, m.nb, w, 1)));
+            MTP_TRY(upload_real(m, &d.Dc1, thread_major(Dt, m.dim, m.nb, nbm, w, 1)));
+            MTP_TRY(upload_real(m, &d.Trc1, thread_major(m.ref.Tr, nv, m.nfb, m.nb, w, 1)));
+            MTP_TRY(upload_real(m, &d.Lc1, thread_major(m.ref.L, nv * nv, m.nb, m.nfb, w, 1)));
+        }
     }
     if (m.precision == MTP_TF32 || m.precision == MTP_TF32X3) {
         const RefTables& r = m.ref;
@@ -225,7 +235,7 @@ int device_mesh_upload(Mesh& m) {
 void device_mesh_free(Mesh& m) {
     if (!m.dev) return;
     DeviceMesh& d = *m.dev;
-    void* ptrs[] = {d.geo, d.elems, d.patch_ptr, d.patch_elem, d.patch_info, d.S, d.Tr, d.L, d.Mc, d.Dc, d.Trc, d.Lc,
+    void* ptrs[] = {d.geo, d.elems, d.patch_ptr, d.patch_elem, d.patch_info, d.S, d.Tr, d.L, d.Mc, d.Dc, d.Trc, d.Lc, d.Mc1, d.Dc1, d.Trc1, d.Lc1,
                     d.V, d.Vinv, d.partial,
                     d.Sf, d.Lfr, d.Trf, d.Sf_lo, d.Lfr_lo, d.Trf_lo};
     for (void* p : ptrs)
@@ -280,16 +290,24 @@ static int device_tents_upload(Tents& t) {
     return MTP_OK;
 }
 
-static const KernelEntry& kernel_entry(const Mesh& m) {
-    static KernelEntry f64[2][5], f32[2][5], tc[2][5], split[2][5];
+static const KernelEntry& kernel_entry(const Mesh& m, int variant = 0) {
+    static KernelEntry f64[2][5], f32[2][5], tc[2][5], split[2][5], rk4[2][5], f32v1[2][5], f32v2[2][5];
     static bool init = false;
     if (!init) {
         kernel_table_f64(f64);
         kernel_table_f32(f32);
         kernel_table_tc(tc);
         kernel_table_split(split);
+        kernel_table_rk4(rk4);
+        kernel_table_f32_v1(f32v1);
+        kernel_table_f32_v2(f32v2);
         init = true;
     }
+    if (variant == 2 && m.precision == MTP_FP32 && !(m.flags & MTP_FLAG_SUBSTITUTED_RK4))
+        return f32v2[m.dim - 2][m.p - 1];
+    if (variant == 1 && m.precision == MTP_FP32 && !(m.flags & MTP_FLAG_SUBSTITUTED_RK4))
+        return f32v1[m.dim - 2][m.p - 1];
+    if (m.flags & MTP_FLAG_SUBSTITUTED_RK4) return rk4[m.dim - 2][m.p - 1];   // FP64 only (checked at creation)
     if (m.precision == MTP_FP32_SPLIT) return split[m.dim - 2][m.p - 1];
     if (m.precision == MTP_TF32 || m.precision == MTP_TF32X3)
         return tc[m.precision == MTP_TF32 ? 0 : 1][m.p - 1];
@@ -455,6 +473,12 @@ static void fill_args(Tents& t, void* state, KArgs& a) {
     a.Dc = dm.Dc;
     a.Trc = dm.Trc;
     a.Lc = dm.Lc;
+    if (t.variant == 2) {   // one row per thread: tables laid out with one row group per matrix row
+        a.Mc = dm.Mc1;
+        a.Dc = dm.Dc1;
+        a.Trc = dm.Trc1;
+        a.Lc = dm.Lc1;
+    }
     a.Sf = (const float4*)dm.Sf;
     a.Lfr = (const float4*)dm.Lfr;
     a.Trf = (const float4*)dm.Trf;
@@ -475,7 +499,7 @@ static void fill_args(Tents& t, void* state, KArgs& a) {
 }
 
 static int enqueue_layers(Tents& t, const KArgs& a, int64_t lb, int64_t le, cudaStream_t st) {
-    const KernelEntry& ke = kernel_entry(*t.mesh);
+    const KernelEntry& ke = kernel_entry(*t.mesh, t.variant);
     for (int64_t l = lb; l < le; ++l) {
         const int64_t t0 = t.layer_ptr[l];
         const int64_t n = t.layer_ptr[l + 1] - t0;
@@ -510,7 +534,7 @@ int device_evolve(Tents& t, void* state, int64_t lb, int64_t le, bool use_graph,
     Mesh& m = *t.mesh;
     DeviceTents& d = *t.dev;
     cudaStream_t st = (cudaStream_t)stream;
-    const KernelEntry& ke = kernel_entry(m);
+    const KernelEntry& ke = kernel_entry(m, t.variant);
     size_t smem = 0;
     const cudaError_t pe = ke.prepare(m.max_patch, &smem);
     int dev, smem_max;
@@ -657,10 +681,10 @@ int device_adjoint(Tents& t, const void* state0, const void* lamT, void* lam0, d
     static AdjEntry table[2][2][5];
     static bool init = false;
     if (!init) { adjoint_table(table); init = true; }
-    if (m.precision == MTP_FP32_SPLIT)
-        return set_error(MTP_EUNSUPPORTED, "the adjoint runs FP64, FP32 and tensor-core meshes, not MTP_FP32_SPLIT");
+    if (m.precision == MTP_FP32_SPLIT || (m.flags & MTP_FLAG_SUBSTITUTED_RK4))
+        return set_error(MTP_EUNSUPPORTED, "the adjoint runs SAT meshes in FP64, FP32 or a tensor-core mode");
     const AdjEntry& ae = table[m.precision == MTP_FP64 ? 0 : 1][m.dim - 2][m.p - 1];
-    const KernelEntry& ke = kernel_entry(m);
+    const KernelEntry& ke = kernel_entry(m, t.variant);
     size_t smem = 0, smem_f = 0;
     const cudaError_t pa_ = ae.prepare(m.max_patch, &smem);
     const cudaError_t pf_ = ke.prepare(m.max_patch, &smem_f);
@@ -792,6 +816,9 @@ int device_batch_evolve(Batch& b, void* const* states, void* stream) {
     static BatchEntry table[2][2];
     static bool init = false;
     if (!init) { batch_table(table); init = true; }
+    for (Tents* t : b.inst)
+        if (t->mesh->flags & MTP_FLAG_SUBSTITUTED_RK4)
+            return set_error(MTP_EUNSUPPORTED, "batches run SAT meshes; MTP_FLAG_SUBSTITUTED_RK4 is per mesh");
     if (m0.precision == MTP_TF32 || m0.precision == MTP_TF32X3 || m0.precision == MTP_FP32_SPLIT)
         return set_error(MTP_EUNSUPPORTED, "batches run FP64 or FP32 SIMT meshes; tensor-core and split modes are per mesh");
     const BatchEntry& be = table[m0.precision == MTP_FP64 ? 0 : 1][m0.dim - 2];

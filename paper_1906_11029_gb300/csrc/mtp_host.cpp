@@ -477,7 +477,10 @@ int mtp_mesh_create(int dim, int64_t n_verts, const double* vertices, int64_t n_
     if (opts->precision < MTP_FP64 || opts->precision > MTP_FP32_SPLIT) return set_error(MTP_EINVAL, "unknown precision");
     if (tc && dim != 3) return set_error(MTP_EUNSUPPORTED, "tensor-core precisions are built for 3D meshes");
     if (opts->n_rhs < 0 || opts->n_rhs > 4096) return set_error(MTP_EINVAL, "n_rhs must be in 0..4096");
-    if (opts->flags & ~(MTP_FLAG_LAYER_LAUNCHES | MTP_FLAG_TEST_STALL)) return set_error(MTP_EINVAL, "unknown flag bits");
+    if (opts->flags & ~(MTP_FLAG_LAYER_LAUNCHES | MTP_FLAG_TEST_STALL | MTP_FLAG_SUBSTITUTED_RK4))
+        return set_error(MTP_EINVAL, "unknown flag bits");
+    if ((opts->flags & MTP_FLAG_SUBSTITUTED_RK4) && opts->precision != MTP_FP64)
+        return set_error(MTP_EUNSUPPORTED, "MTP_FLAG_SUBSTITUTED_RK4 is built for MTP_FP64");
     auto h = std::make_unique<mtp_mesh>();
     int rc = build_mesh(dim, n_verts, vertices, n_elems, elements, eps, mu, *opts, h->m);
     if (rc != MTP_OK) return rc;
@@ -621,6 +624,16 @@ int mtp_tents_set_launch(mtp_tents_t tents, int launch) {
     if (!tents) return set_error(MTP_EINVAL, "tents is NULL");
     if (launch < 0 || launch > 2) return set_error(MTP_EINVAL, "launch must be 0, 1 or 2");
     tents->t.launch = launch;
+    return MTP_OK;
+}
+
+int mtp_tents_set_variant(mtp_tents_t tents, int variant) {
+    if (!tents) return set_error(MTP_EINVAL, "tents is NULL");
+    if (variant < 0 || variant > 2) return set_error(MTP_EINVAL, "variant must be 0, 1 or 2");
+    const Mesh& m = *tents->t.mesh;
+    if (variant > 0 && (m.precision != MTP_FP32 || (m.flags & MTP_FLAG_SUBSTITUTED_RK4)))
+        return set_error(MTP_EUNSUPPORTED, "kernel variants 1 and 2 are built for MTP_FP32 SAT meshes");
+    tents->t.variant = variant;
     return MTP_OK;
 }
 

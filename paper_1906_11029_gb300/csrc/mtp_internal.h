@@ -81,6 +81,8 @@ struct Tents {
     // evolve launch configuration (see mtp_tents_set_launch): 0 DAG walk at the occupancy
     // limit of CTAs per SM, 1 DAG walk with one CTA per SM, 2 one launch per layer
     int launch = 0;
+    // kernel shape variant (see mtp_tents_set_variant): 0 paired elements, 1 one element per item
+    int variant = 0;
     struct DeviceTents* dev = nullptr;
 };
 

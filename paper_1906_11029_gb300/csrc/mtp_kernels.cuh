@@ -84,8 +84,18 @@ __host__ __device__ constexpr int degree_of(int dim, int r) {
     return k;
 }
 
-template <int DIM, int P>
+// Kernel shape variants travel in the degree template argument as PV = p + 16 v.
+// v = 0 (default): an FP32 stage item covers a pair of patch elements with the same local index
+// of V (they share every table read); v = 1: one element per item, twice the items at half
+// the work each, which shortens a tent when the layers have fewer tents than the GPU has CTA
+// slots (3D, 512 threads per CTA from p = 4 so that a 24-element patch still fits one round);
+// v = 2: one element and one basis function (or facet mode) per item, 512 threads per CTA in
+// 3D: every phase of a 24-element p <= 3 patch in one round at a quarter of the default's
+// per-thread work, for the shortest tents on latency-bound layers.
+template <int DIM, int PV>
 struct Shape {
+    static constexpr int P = PV & 15, V = PV >> 4;
+    static constexpr bool PAIRS = V == 0;                 // FP32 items pair elements (FP64 never)
     static constexpr int NF = DIM == 2 ? 3 : 6;
     static constexpr int NB = DIM == 2 ? (P + 1) * (P + 2) / 2 : (P + 1) * (P + 2) * (P + 3) / 6;
     static constexpr int NFB = DIM == 2 ? P + 1 : (P + 1) * (P + 2) / 2;
@@ -93,8 +103,8 @@ struct Shape {
     static constexpr int NFBP = pad4(NFB);
     static constexpr int GIS = pad4(NF);                  // row stride of G^-1 in shared memory
     static constexpr int NV = DIM + 1;
-    static constexpr int NT = DIM == 2 ? 128 : 256;   // threads per CTA
-    static constexpr int AP = 2;                       // basis functions per thread
+    static constexpr int NT = DIM == 2 ? 128 : ((V == 1 && P >= 4) || V == 2 ? 512 : 256);   // threads per CTA
+    static constexpr int AP = V == 2 ? 1 : 2;          // basis functions (facet modes) per thread
     static constexpr int NAG = (NB + AP - 1) / AP;     // basis groups per element
     static constexpr int NCG = (NFB + AP - 1) / AP;    // facet-mode groups per facet
     // Degree structure of the tables (basis ordered by degree): S[a][b] = 0 for deg b > deg a
@@ -123,9 +133,10 @@ struct Shape {
 
 // CTAs per SM the register budget is shaped for (two 256-thread CTAs fit the FP32 3D
 // shared-memory footprint up to p = 4; FP64 p >= 3 fits one)
-template <typename Real, int DIM, int P>
+template <typename Real, int DIM, int PV>
 struct MinBlocks {
-    static constexpr int value = ((sizeof(Real) == 4 && P <= 4) || P <= 2) ? 2 : 1;
+    static constexpr int P = Shape<DIM, PV>::P;
+    static constexpr int value = Shape<DIM, PV>::NT > 256 ? 1 : (((sizeof(Real) == 4 && P <= 4) || P <= 2) ? 2 : 1);
 };
 
 template <typename Real>
@@ -143,14 +154,31 @@ struct Vec<double> {
     static __device__ __forceinline__ void get(const T& v, double o[2]) { o[0] = v.x; o[1] = v.y; }
 };
 
+// Shared-memory strides of the per-element blocks that threads of one warp access for
+// different elements: facet traces / fluxes (FSZ per facet, TSZ per element) and G^-1 (GSZ per
+// element) are padded so that the facets of one element and elements one or two slots apart
+// start in different shared-memory banks (BANKW = banks per bank row in units of Real).
+template <typename Real, int DIM, int P>
+struct Strides {
+    using Sh = Shape<DIM, P>;
+    static constexpr int BANKW = 32 * 4 / (int)sizeof(Real);
+    static constexpr int up_to(int x, int r) { return x + ((r - x % BANKW) % BANKW + BANKW) % BANKW; }
+    static constexpr int FSZ = up_to(Sh::NF * Sh::NFBP, BANKW / 2);
+    static constexpr int TSZ = up_to(DIM * FSZ, 3 * BANKW / 4);
+    static constexpr int GSZ = (Sh::NF * Sh::GIS) % (BANKW / 2) == 0 ? Sh::NF * Sh::GIS + 4 : Sh::NF * Sh::GIS;
+};
+
 // MODE 0: SIMT contractions in the state precision; 1: TF32 tensor-core MMAs (FP32 state,
 // FP32 accumulate); 2: the same with a 3-term hi + lo split of both operands; 3: SIMT FP32
 // contractions with the Taylor sum carried as an FP32 pair hi + lo (two-sum) and an FP64
-// state between tents.
+// state between tents; 4: SIMT contractions, but the tent ODE advanced by the classical
+// Runge-Kutta method on the substituted equation d/dt Y = A M^-1 Y instead of SAT (the
+// approach Sec. 3 contrasts with SAT; a negative control for convergence studies).
 template <int MODE>
 struct ModeTraits {
-    static constexpr bool simt = MODE == 0 || MODE == 3;
+    static constexpr bool simt = MODE == 0 || MODE == 3 || MODE == 4;
     static constexpr bool split = MODE == 3;
+    static constexpr bool rk4 = MODE == 4;
 };
 template <typename Real, int MODE>
 using StateOf = typename std::conditional<ModeTraits<MODE>::split, double, Real>::type;
@@ -162,23 +190,24 @@ struct SmemLayout {
     static __host__ __device__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
     size_t off_Y, off_Ylo, off_Ua, off_Ub, off_W, off_tr, off_Gi, off_gphi, off_gdel, off_mat, off_ac, off_gd,
         off_nrm, off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, off_pair, off_own, bytes, state_bytes, tr_bytes;
-    bool split, factored, twobuf;
+    bool split, factored, twobuf, rk4;   // rk4: Y at the sub-step start (Ylo slot), stage input (Ub)
     // mode (see ModeTraits): split carries the Taylor accumulator Y as an unevaluated pair
     // hi + lo (one more patch-state buffer); the SIMT modes use the factored volume term (a W
     // buffer) and update U in place, the tensor-core modes keep two U buffers (twobuf also
     // asks for the second one, for the adjoint's reverse recursion)
     __host__ __device__ explicit SmemLayout(int mp, int mode = 0, bool two = false)
-        : split(mode == 3), factored(mode == 0 || mode == 3), twobuf(two || !(mode == 0 || mode == 3)) {
+        : split(mode == 3), factored(mode == 0 || mode == 3 || mode == 4),
+          twobuf(two || mode == 1 || mode == 2 || mode == 4), rk4(mode == 4) {
         size_t o = 0;
         state_bytes = (size_t)mp * Sh::NF * Sh::NBP * sizeof(Real);
-        tr_bytes = (size_t)mp * DIM * Sh::NF * Sh::NFBP * sizeof(Real);
+        tr_bytes = (size_t)mp * Strides<Real, DIM, P>::TSZ * sizeof(Real);
         off_Y = o; o = align16(o + state_bytes);
-        off_Ylo = o; if (split) o = align16(o + state_bytes);
+        off_Ylo = o; if (split || rk4) o = align16(o + state_bytes);
         off_Ua = o; o = align16(o + state_bytes);
         off_Ub = o; if (twobuf) o = align16(o + state_bytes);
         off_W = o; if (factored) o = align16(o + (size_t)mp * Sh::NF * Sh::NBMP * sizeof(Real));
         off_tr = o; o = align16(o + tr_bytes);
-        off_Gi = o; o = align16(o + (size_t)mp * Sh::NF * Sh::GIS * sizeof(Real));
+        off_Gi = o; o = align16(o + (size_t)mp * Strides<Real, DIM, P>::GSZ * sizeof(Real));
         off_gphi = o; o = align16(o + (size_t)mp * 3 * sizeof(double));
         off_gdel = o; o = align16(o + (size_t)mp * 3 * sizeof(double));
         off_mat = o; o = align16(o + (size_t)mp * 2 * sizeof(double));
@@ -237,6 +266,7 @@ template <typename Real, int DIM, int P>
 struct TentCtx {
     using Sh = Shape<DIM, P>;
     Real *sY, *sYlo, *sUa, *sUb, *sW, *sTr, *sGi;   // sYlo / sUb / sW null when the layout has none
+    Real* sY0;                                     // RK4 mode: Y at the start of the sub-step
     double *sGphi, *sGdel, *sMat;
     Real *sAc, *sGd, *sNrm, *sLiftc, *sTrs, *sZ;
     int8_t *sJ, *sNslot, *sNfi, *sPair;   // sPair: [pair][2] element slots (second -1: single)
@@ -250,6 +280,7 @@ struct TentCtx {
     __device__ void carve(unsigned char* smem, const SmemLayout<Real, DIM, P>& lay) {
         sY = (Real*)(smem + lay.off_Y);
         sYlo = lay.split ? (Real*)(smem + lay.off_Ylo) : nullptr;
+        sY0 = lay.rk4 ? (Real*)(smem + lay.off_Ylo) : nullptr;
         sUa = (Real*)(smem + lay.off_Ua);
         sUb = lay.twobuf ? (Real*)(smem + lay.off_Ub) : nullptr;
         sW = lay.factored ? (Real*)(smem + lay.off_W) : nullptr;
@@ -283,7 +314,7 @@ template <typename Real, int DIM, int P, bool CG = false, typename SrcT = Real>
 __device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t tent, const SrcT* src) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NV = Sh::NV, NT = Sh::NT, NBP = Sh::NBP;
-    constexpr int ESZ = NF * NBP, TSZ = DIM * NF * Sh::NFBP;
+    constexpr int ESZ = NF * NBP, TSZ = Strides<Real, DIM, P>::TSZ;
     const int tid = threadIdx.x;
     c.V = a.tent_v[tent];
     c.tb = a.tent_tb[tent];
@@ -390,11 +421,13 @@ __device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t ten
 // one row per thread, in the state precision.  The causality test |g| < sqrt(eps mu) at
 // t_i (and at the tent top when i = 0) decides an error and is taken in FP64.
 template <typename Real, int DIM, int P>
-__device__ void tent_ginv(TentCtx<Real, DIM, P>& c, const KArgs& a, int i) {
+__device__ void tent_ginv_into(TentCtx<Real, DIM, P>& c, const KArgs& a, double ti, bool check_top, Real* dst,
+                               int t0, int nthr) {
     using Sh = Shape<DIM, P>;
-    constexpr int NF = Sh::NF, NT = Sh::NT;
-    const double ti = (double)i / (double)a.m;
-    for (int k = threadIdx.x; k < c.ns; k += NT) {
+    constexpr int NF = Sh::NF;
+    const int me = (int)threadIdx.x - t0;
+    if (me < 0) return;
+    for (int k = me; k < c.ns; k += nthr) {
         const double eps = c.sMat[2 * k], mu = c.sMat[2 * k + 1];
         double gg = 0;
         for (int q = 0; q < 3; ++q) {
@@ -402,7 +435,7 @@ __device__ void tent_ginv(TentCtx<Real, DIM, P>& c, const KArgs& a, int i) {
             gg += g * g;
         }
         if (!(gg < eps * mu)) atomicCAS(a.err, 0, 1);
-        if (i == 0) {   // grad phi is affine in t, so bottom and top bound the whole tent
+        if (check_top) {   // grad phi is affine in t, so bottom and top bound the whole tent
             double gt = 0;
             for (int q = 0; q < 3; ++q) {
                 const double g = c.sGphi[3 * k + q] + c.sGdel[3 * k + q];
@@ -412,7 +445,7 @@ __device__ void tent_ginv(TentCtx<Real, DIM, P>& c, const KArgs& a, int i) {
         }
     }
     const Real tr = (Real)ti;
-    for (int idx = threadIdx.x; idx < c.ns * NF; idx += NT) {
+    for (int idx = me; idx < c.ns * NF; idx += nthr) {
         const int k = idx / NF, R = field6<DIM>(idx - k * NF);
         Real g[3];
 #pragma unroll
@@ -431,10 +464,21 @@ __device__ void tent_ginv(TentCtx<Real, DIM, P>& c, const KArgs& a, int i) {
             row[R < 3 ? q : 3 + q] = diag;
             row[R < 3 ? 3 + q : q] = sx * cr;
         }
-        Real* out = c.sGi + idx * Sh::GIS;
+        Real* out = dst + k * Strides<Real, DIM, P>::GSZ + (idx - k * NF) * Sh::GIS;
 #pragma unroll
         for (int q = 0; q < NF; ++q) out[q] = row[field6<DIM>(q)];
     }
+}
+
+template <typename Real, int DIM, int P>
+__device__ __forceinline__ void tent_ginv_at(TentCtx<Real, DIM, P>& c, const KArgs& a, double ti, bool check_top) {
+    tent_ginv_into(c, a, ti, check_top, c.sGi, 0, (int)blockDim.x);
+}
+
+// G(t_i)^-1 at the start of sub-interval i (the tent bottom and top are checked at i = 0)
+template <typename Real, int DIM, int P>
+__device__ __forceinline__ void tent_ginv(TentCtx<Real, DIM, P>& c, const KArgs& a, int i) {
+    tent_ginv_at(c, a, (double)i / (double)a.m, i == 0);
 }
 
 // Error-free sum of two floats (Knuth's two-sum): hi + lo == a + b exactly, hi = fl(a + b).
@@ -464,7 +508,7 @@ __device__ void tent_apply_ginv(TentCtx<Real, DIM, P>& c, Real* src, Real* dst) 
     constexpr int NF = Sh::NF, NB = Sh::NB, ESZ = NF * Sh::NBP, NBP = Sh::NBP, GIS = Sh::GIS;
     for (int idx = threadIdx.x; idx < c.ns * NB; idx += blockDim.x) {
         const int k = idx / NB, b = idx - k * NB;
-        const Real* Gi = c.sGi + k * NF * GIS;
+        const Real* Gi = c.sGi + k * Strides<Real, DIM, P>::GSZ;
         Real y[NF];
 #pragma unroll
         for (int s = 0; s < NF; ++s) {
@@ -496,7 +540,7 @@ __device__ __forceinline__ void tent_w_item(TentCtx<Real, DIM, P>& c, const KArg
     using VT = typename Vec<Real>::T;
     constexpr int NF = Sh::NF, NBP = Sh::NBP, NBM = Sh::NBM, NBMP = Sh::NBMP, NWG = Sh::NWG;
     constexpr int AP = Sh::AP, W = Vec<Real>::W, ESZ = NF * NBP, WSZ = NF * NBMP;
-    constexpr int EP = sizeof(Real) == 4 ? 2 : 1;
+    constexpr int EP = (sizeof(Real) == 4 && Sh::PAIRS) ? 2 : 1;
     constexpr int WMAT = NBP * AP * NWG;
     const int pi = w / NWG, g = w - pi * NWG;
     const int k0 = EP == 2 ? c.sPair[2 * pi] : pi;
@@ -512,7 +556,7 @@ __device__ __forceinline__ void tent_w_item(TentCtx<Real, DIM, P>& c, const KArg
             for (int s = 0; s < NF; ++s) acc[e][ci][s] = 0;
     // column block [b, b + W): rows R0 <= ci < R1
     auto block = [&](int b, auto r0, auto r1) {
-        constexpr int R0 = decltype(r0)::value, R1 = decltype(r1)::value;
+        constexpr int R0 = decltype(r0)::value, R1 = decltype(r1)::value < AP ? decltype(r1)::value : AP;
         Real mv[AP][W];
 #pragma unroll
         for (int ci = R0; ci < R1; ++ci) Vec<Real>::get(__ldg((const VT*)(Mg + b * AP * NWG + ci * NWG * W)), mv[ci]);
@@ -565,7 +609,7 @@ template <typename Real, int DIM, int P>
 __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real* Ucur, Real* tr) {
     if (c.sW) {
         constexpr int NT = Shape<DIM, P>::NT;
-        const int nitems = (sizeof(Real) == 4 ? *c.sNpair : c.ns) * Shape<DIM, P>::NWG;
+        const int nitems = ((sizeof(Real) == 4 && Shape<DIM, P>::PAIRS) ? *c.sNpair : c.ns) * Shape<DIM, P>::NWG;
         const int busy = (c.ns * Shape<DIM, P>::NCG) % NT, idle = NT - busy;
         if ((int)threadIdx.x >= busy)
             for (int w = threadIdx.x - busy; w < nitems; w += idle) tent_w_item(c, a, Ucur, w);
@@ -573,7 +617,7 @@ __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real
     using Sh = Shape<DIM, P>;
     using VT = typename Vec<Real>::T;
     constexpr int NF = Sh::NF, NFB = Sh::NFB, NT = Sh::NT, NBP = Sh::NBP, NFBP = Sh::NFBP;
-    constexpr int AP = Sh::AP, NCG = Sh::NCG, W = Vec<Real>::W, ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
+    constexpr int AP = Sh::AP, NCG = Sh::NCG, W = Vec<Real>::W, ESZ = NF * NBP, TSZ = Strides<Real, DIM, P>::TSZ, FSZ = Strides<Real, DIM, P>::FSZ;
     constexpr int TMAT = NBP * AP * NCG;   // one thread-major facet table
     const Real* Tr = (const Real*)a.Trc;
     for (int idx = threadIdx.x; idx < c.ns * NCG; idx += NT) {
@@ -616,42 +660,50 @@ __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real
                         for (int ci = 0; ci < NR; ++ci) acc[fi][ci][s] += tv[fi][ci][v] * u[v];
             }
         };
-        constexpr int BT = Sh::TLO / W * W;   // second rows vanish on the blocks below
+        if constexpr (AP == 1) {
 #pragma unroll 1
-        for (int b = 0; b < BT; b += W) block(b, std::integral_constant<int, 1>{});
+            for (int b = 0; b < NBP; b += W) block(b, std::integral_constant<int, 1>{});
+        } else {
+            constexpr int BT = Sh::TLO / W * W;   // second rows vanish on the blocks below
 #pragma unroll 1
-        for (int b = BT; b < NBP; b += W) block(b, std::integral_constant<int, 2>{});
+            for (int b = 0; b < BT; b += W) block(b, std::integral_constant<int, 1>{});
+#pragma unroll 1
+            for (int b = BT; b < NBP; b += W) block(b, std::integral_constant<int, 2>{});
+        }
         const Real sc = c.sTrs[k];
 #pragma unroll
         for (int fi = 0; fi < DIM; ++fi) {
-            Real* out = tr + k * TSZ + fi * NF * NFBP + cg;
+            Real* out = tr + k * TSZ + fi * FSZ + cg;
 #pragma unroll
             for (int s = 0; s < NF; ++s) {
                 out[s * NFBP] = acc[fi][0][s] * sc;
-                if (two) out[s * NFBP + NCG] = acc[fi][1][s] * sc;
+                if constexpr (AP == 2)
+                    if (two) out[s * NFBP + NCG] = acc[fi][AP - 1][s] * sc;
             }
         }
     }
 }
 
 // (b2) numerical flux, once per facet (lower slot owns an interior facet), in place in tr,
-// pre-scaled by each side's lift factor dt (d-1)!|F| / sqrt|det J|
+// pre-scaled by each side's lift factor dt (d-1)!|F| / sqrt|det J|; one thread per (facet,
+// facet mode)
 template <typename Real, int DIM, int P>
 __device__ void tent_fluxes(TentCtx<Real, DIM, P>& c, Real* tr) {
     using Sh = Shape<DIM, P>;
-    constexpr int NF = Sh::NF, NFB = Sh::NFB, NFBP = Sh::NFBP, TSZ = DIM * NF * NFBP;
+    constexpr int NF = Sh::NF, NFB = Sh::NFB, NFBP = Sh::NFBP, TSZ = Strides<Real, DIM, P>::TSZ, FSZ = Strides<Real, DIM, P>::FSZ;
     const int nown = *c.sNown;
-    for (int idx = threadIdx.x; idx < nown * NFB; idx += blockDim.x) {
+    const int nitems = nown * NFB;
+    for (int idx = threadIdx.x; idx < nitems; idx += blockDim.x) {
         const int oi = idx / NFB, cc = idx - oi * NFB;
         const int k = c.sOwn[2 * oi], fi = c.sOwn[2 * oi + 1];
         const int s2 = c.sNslot[k * DIM + fi];
-        Real* mine = tr + k * TSZ + fi * NF * NFBP + cc;
+        Real* mine = tr + k * TSZ + fi * FSZ + cc;
         Real um[6] = {0, 0, 0, 0, 0, 0}, up[6] = {0, 0, 0, 0, 0, 0}, F[6], nrm[3];
 #pragma unroll
         for (int s = 0; s < NF; ++s) um[field6<DIM>(s)] = mine[s * NFBP];
         Real* other = nullptr;
         if (s2 >= 0) {
-            other = tr + s2 * TSZ + c.sNfi[k * DIM + fi] * NF * NFBP + cc;
+            other = tr + s2 * TSZ + c.sNfi[k * DIM + fi] * FSZ + cc;
 #pragma unroll
             for (int s = 0; s < NF; ++s) up[field6<DIM>(s)] = other[s * NFBP];
         } else {
@@ -675,14 +727,18 @@ __device__ void tent_fluxes(TentCtx<Real, DIM, P>& c, Real* tr) {
 // accumulation into sY, and U_{i,n} = G_i^-1 (Y_{i,n} - n M' U_{i,n-1}) into Unext (n < q).
 // One thread per (pair of elements with the same local index j, two basis functions): every
 // 16-byte read of the j-dependent tables S and L feeds both elements.
-template <typename Real, int DIM, int P, bool SPLIT = false>
+// EPI 0: SAT (Taylor accumulation and the next U); 1: SAT with the split accumulator;
+// 2: RK4 stage on d/dt Y = A M^-1 Y: K = A U, Y += rk_w K, and (rk_c > 0) the next stage input
+// Unext = Y_start + rk_c K (a Y-space value; the caller solves for U)
+template <typename Real, int DIM, int P, int EPI = 0>
 __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, const Real* Ucur, Real* Unext,
-                           const Real* tr) {
+                           const Real* tr, Real rk_w = 0, Real rk_c = 0) {
+    constexpr bool SPLIT = EPI == 1;
     using Sh = Shape<DIM, P>;
     using VT = typename Vec<Real>::T;
     constexpr int NF = Sh::NF, NB = Sh::NB, NV = Sh::NV, NT = Sh::NT, NBP = Sh::NBP, NFBP = Sh::NFBP;
-    constexpr int AP = Sh::AP, NAG = Sh::NAG, W = Vec<Real>::W, ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
-    constexpr int EP = sizeof(Real) == 4 ? 2 : 1;   // elements per thread (FP64: register budget)
+    constexpr int AP = Sh::AP, NAG = Sh::NAG, W = Vec<Real>::W, ESZ = NF * NBP, TSZ = Strides<Real, DIM, P>::TSZ, FSZ = Strides<Real, DIM, P>::FSZ;
+    constexpr int EP = (sizeof(Real) == 4 && Sh::PAIRS) ? 2 : 1;   // elements per item (FP64: register budget)
     constexpr int NBMP = Sh::NBMP, WSZ = NF * NBMP;
     constexpr int DMAT = NBMP * AP * NAG, LMAT = NFBP * AP * NAG;   // thread-major D^T and L matrices
     const Real* Lf = (const Real*)a.Lc;
@@ -793,21 +849,21 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
                     for (int s = 0; s < NF; ++s) acc[e][ai][s] = 0;
 #pragma unroll
             for (int cc = 0; cc < NFBP; cc += W) {
-                Real l0[W], l1[W];
-                Vec<Real>::get(__ldg((const VT*)(Lg + cc * AP * NAG)), l0);
-                Vec<Real>::get(__ldg((const VT*)(Lg + cc * AP * NAG + NAG * W)), l1);
+                Real lv[AP][W];
+#pragma unroll
+                for (int ai = 0; ai < AP; ++ai)
+                    Vec<Real>::get(__ldg((const VT*)(Lg + cc * AP * NAG + ai * NAG * W)), lv[ai]);
 #pragma unroll
                 for (int e = 0; e < EP; ++e) {
-                    const Real* Fx = tr + kk[e] * TSZ + fi * NF * NFBP;
+                    const Real* Fx = tr + kk[e] * TSZ + fi * FSZ;
 #pragma unroll
                     for (int s = 0; s < NF; ++s) {
                         Real fv[W];
                         Vec<Real>::get(*(const VT*)(Fx + s * NFBP + cc), fv);
 #pragma unroll
-                        for (int v = 0; v < W; ++v) {
-                            acc[e][0][s] += l0[v] * fv[v];
-                            acc[e][1][s] += l1[v] * fv[v];
-                        }
+                        for (int v = 0; v < W; ++v)
+#pragma unroll
+                            for (int ai = 0; ai < AP; ++ai) acc[e][ai][s] += lv[ai][v] * fv[v];
                     }
                 }
             }
@@ -824,11 +880,20 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
             const int k = kk[e];
             const Real* U = Ucur + k * ESZ;
             const Real* gd = c.sGd + 3 * k;
-            const Real* Gi = c.sGi + k * NF * Sh::GIS;
+            const Real* Gi = c.sGi + k * Strides<Real, DIM, P>::GSZ;
 #pragma unroll
             for (int ai = 0; ai < AP; ++ai) {
                 if (ai == 1 && !two) break;
                 const int av = ag + ai * NAG;
+                if constexpr (EPI == 2) {
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) {
+                        const int i = k * ESZ + s * NBP + av;
+                        c.sY[i] += rk_w * Yn[e][ai][s];
+                        if (rk_c != Real(0)) Unext[i] = c.sY0[i] + rk_c * Yn[e][ai][s];
+                    }
+                    continue;
+                }
                 if constexpr (SPLIT) {
 #pragma unroll
                     for (int s = 0; s < NF; ++s) {   // (hi, lo) += cn Yn: two-sum, error into lo
@@ -892,31 +957,77 @@ template <typename Real, int DIM, int P, int MODE>
 __device__ void tent_stage_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, const Real* Ucur, Real* Unext,
                               const Real* tr);
 
-template <typename Real, int DIM, int P, int MODE = 0>
-__device__ void tent_sat(TentCtx<Real, DIM, P>& c, const KArgs& a, Real* tape) {
+// Classical RK4 with m steps on the substituted tent ODE d/dt Y = A M(t)^-1 Y (Sec. 3, after
+// eq. equ_ode): per step with start t0 and size h = 1/m, stages at t0, t0 + h/2, t0 + h/2, t0 + h
+// with weights 1/6, 1/3, 1/3, 1/6; each stage solves U = M(t_s)^-1 Y_s and applies A.
+template <typename Real, int DIM, int P>
+__device__ void tent_rk4(TentCtx<Real, DIM, P>& c, const KArgs& a) {
     constexpr int ESZ = Shape<DIM, P>::NF * Shape<DIM, P>::NBP;
-    const size_t slot = (size_t)a.max_patch * ESZ;
+    const double h = 1.0 / (double)a.m;
+    const double toff[4] = {0.0, 0.5, 0.5, 1.0}, wts[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
+    const double cns[4] = {0.5, 0.5, 1.0, 0.0};
+    Real* Ys = c.sUb;                                  // stage input (Y space)
     for (int i = 0; i < a.m; ++i) {
-        tent_ginv(c, a, i);
-        if (tape) tent_copy<Real, DIM, P>(c.ns, c.sY, tape + (size_t)i * slot);
-        __syncthreads();
-        // SIMT modes update U in place (the factored stage reads only its own rows of U);
-        // the tensor-core stages read all of U while writing the next one
-        Real* Ucur = c.sUa;
-        Real* Unext = ModeTraits<MODE>::simt ? c.sUa : c.sUb;
-        tent_apply_ginv(c, c.sY, Ucur);
-        __syncthreads();
-        for (int n = 1; n <= a.q; ++n) {
-            if (tape) tent_copy<Real, DIM, P>(c.ns, Ucur, tape + (size_t)(a.m + i * a.q + n - 1) * slot);
-            if constexpr (ModeTraits<MODE>::simt) tent_traces(c, a, Ucur, c.sTr);
-            else tent_traces_tc<Real, DIM, P, MODE>(c, a, Ucur, c.sTr);
+        for (int idx = threadIdx.x; idx < c.ns * ESZ; idx += blockDim.x) c.sY0[idx] = c.sY[idx];
+        for (int st = 0; st < 4; ++st) {
+            tent_ginv_at(c, a, ((double)i + toff[st]) * h, i == 0 && st == 0);
+            __syncthreads();
+            tent_apply_ginv(c, st == 0 ? c.sY0 : Ys, c.sUa);
+            __syncthreads();
+            tent_traces(c, a, c.sUa, c.sTr);
             __syncthreads();
             tent_fluxes(c, c.sTr);
             __syncthreads();
-            if constexpr (ModeTraits<MODE>::simt) tent_stage<Real, DIM, P, ModeTraits<MODE>::split>(c, a, n, Ucur, Unext, c.sTr);
-            else tent_stage_tc<Real, DIM, P, MODE>(c, a, n, Ucur, Unext, c.sTr);
+            tent_stage<Real, DIM, P, 2>(c, a, 1, c.sUa, Ys, c.sTr, (Real)(wts[st] * h), (Real)(cns[st] * h));
             __syncthreads();
-            if constexpr (!ModeTraits<MODE>::simt) {
+        }
+    }
+}
+
+template <typename Real, int DIM, int P, int MODE = 0>
+__device__ void tent_sat(TentCtx<Real, DIM, P>& c, const KArgs& a, Real* tape) {
+    if constexpr (ModeTraits<MODE>::rk4) {
+        tent_rk4(c, a);
+        return;
+    }
+    constexpr int ESZ = Shape<DIM, P>::NF * Shape<DIM, P>::NBP;
+    const size_t slot = (size_t)a.max_patch * ESZ;
+    if constexpr (ModeTraits<MODE>::simt) {
+        // U is updated in place: the factored stage reads only its own rows of U
+        Real* U = c.sUa;
+        for (int i = 0; i < a.m; ++i) {
+            tent_ginv(c, a, i);
+            if (tape) tent_copy<Real, DIM, P>(c.ns, c.sY, tape + (size_t)i * slot);
+            __syncthreads();
+            tent_apply_ginv(c, c.sY, U);
+            __syncthreads();
+            for (int n = 1; n <= a.q; ++n) {
+                if (tape) tent_copy<Real, DIM, P>(c.ns, U, tape + (size_t)(a.m + i * a.q + n - 1) * slot);
+                tent_traces(c, a, U, c.sTr);
+                __syncthreads();
+                tent_fluxes(c, c.sTr);
+                __syncthreads();
+                tent_stage<Real, DIM, P, ModeTraits<MODE>::split ? 1 : 0>(c, a, n, U, U, c.sTr);
+                __syncthreads();
+            }
+        }
+    } else {
+        for (int i = 0; i < a.m; ++i) {
+            tent_ginv(c, a, i);
+            if (tape) tent_copy<Real, DIM, P>(c.ns, c.sY, tape + (size_t)i * slot);
+            __syncthreads();
+            Real* Ucur = c.sUa;
+            Real* Unext = c.sUb;
+            tent_apply_ginv(c, c.sY, Ucur);
+            __syncthreads();
+            for (int n = 1; n <= a.q; ++n) {
+                if (tape) tent_copy<Real, DIM, P>(c.ns, Ucur, tape + (size_t)(a.m + i * a.q + n - 1) * slot);
+                tent_traces_tc<Real, DIM, P, MODE>(c, a, Ucur, c.sTr);
+                __syncthreads();
+                tent_fluxes(c, c.sTr);
+                __syncthreads();
+                tent_stage_tc<Real, DIM, P, MODE>(c, a, n, Ucur, Unext, c.sTr);
+                __syncthreads();
                 Real* tmp = Ucur; Ucur = Unext; Unext = tmp;
             }
         }
@@ -1166,7 +1277,7 @@ __device__ void tent_traces_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, const R
     using Sh = Shape<DIM, P>;
     using Tc = TcShape<P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NFB = Sh::NFB, NBP = Sh::NBP, NFBP = Sh::NFBP;
-    constexpr int ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
+    constexpr int ESZ = NF * NBP, TSZ = Strides<Real, DIM, P>::TSZ, FSZ = Strides<Real, DIM, P>::FSZ;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const int npair = *c.sNpair;
@@ -1195,7 +1306,7 @@ __device__ void tent_traces_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, const R
             if (nt == 1 && kk1 < 0) break;
             const int k = ke[nt];
             const Real sc = c.sTrs[k];
-            Real* out = tr + k * TSZ + fi * NF * NFBP;
+            Real* out = tr + k * TSZ + fi * FSZ;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int cc = g + 8 * h;
@@ -1215,7 +1326,7 @@ __device__ void tent_stage_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, c
     using Sh = Shape<DIM, P>;
     using Tc = TcShape<P>;
     constexpr int NF = Sh::NF, NB = Sh::NB, NFB = Sh::NFB, NBP = Sh::NBP, NFBP = Sh::NFBP, NV = Sh::NV;
-    constexpr int ESZ = NF * NBP, TSZ = DIM * NF * NFBP;
+    constexpr int ESZ = NF * NBP, TSZ = Strides<Real, DIM, P>::TSZ, FSZ = Strides<Real, DIM, P>::FSZ;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const unsigned full = 0xffffffffu;
@@ -1259,7 +1370,7 @@ __device__ void tent_stage_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, c
 #pragma unroll
                 for (int nt = 0; nt < 2; ++nt) {
                     uint32_t bh[2], bl[2];
-                    load_b<MODE>(tr + ke[nt] * TSZ + fi * NF * NFBP + g * NFBP, g < NF, 8 * kt + t, NFB, bh, bl);
+                    load_b<MODE>(tr + ke[nt] * TSZ + fi * FSZ + g * NFBP, g < NF, 8 * kt + t, NFB, bh, bl);
                     mma_mode<MODE>(Lc[nt], ah, al, bh, bl);
                 }
             }
@@ -1272,7 +1383,7 @@ __device__ void tent_stage_tc(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, c
             const float* ac = c.sAc + k * DIM * 3;
             const float* U = Ucur + k * ESZ;
             const float* gd = c.sGd + 3 * k;
-            const float* Gi = c.sGi + k * NF * Sh::GIS;
+            const float* Gi = c.sGi + k * Strides<Real, DIM, P>::GSZ;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int av = 16 * mt + g + 8 * h;

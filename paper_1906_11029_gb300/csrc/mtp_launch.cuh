@@ -72,6 +72,12 @@ void kernel_table_f32(KernelEntry entries[2][5]);
 void kernel_table_tc(KernelEntry entries[2][5]);
 // FP32 arithmetic with the split (hi + lo) Taylor accumulator and an FP64 state: entries[dim - 2][p - 1]
 void kernel_table_split(KernelEntry entries[2][5]);
+// FP64, classical RK4 on the substituted tent ODE instead of SAT (MTP_FLAG_SUBSTITUTED_RK4)
+void kernel_table_rk4(KernelEntry entries[2][5]);
+// FP32, kernel shape variants 1 (one element per stage item) and 2 (one element and one row
+// per item, 512 threads); see Shape
+void kernel_table_f32_v1(KernelEntry entries[2][5]);
+void kernel_table_f32_v2(KernelEntry entries[2][5]);
 
 struct AdjArgs;
 using AdjLaunchFn = cudaError_t (*)(const AdjArgs&, int64_t t0, int n_tents, int n_rhs, cudaStream_t st);

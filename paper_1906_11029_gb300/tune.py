@@ -7,7 +7,12 @@ Two levels:
   with the occupancy limit of CTAs per SM, DAG walk with one CTA per SM, or one launch per layer;
 * contraction variant within an accuracy class (here): for FP32-level accuracy the SIMT FP32
   kernels or the tensor-core 3xTF32 split; for "tf32" accuracy additionally plain TF32 tensor
-  cores.  Variants are timed on the same layer window of the caller's workload.
+  cores;
+* kernel shape of the SIMT FP32 kernels (here, `mtp_tents_set_variant`): stage items over pairs
+  of patch elements (variant 0), single elements (variant 1) or single (element, row) pairs on
+  512 threads (variant 2): more and shorter items, faster tents when the layers hold fewer
+  tents than the GPU has CTA slots.
+Candidates are timed on the same layer window of the caller's workload.
 
 Choices are cached in a JSON file (default ``~/.cache/paper_1906_11029_gb300/tune.json``)
 keyed by GPU name, dimension, degree, accuracy class, largest patch size and the workload's
@@ -54,17 +59,20 @@ def _save(path, data):
 
 
 def candidates(dim, p, accuracy):
-    """Precision variants that the library compiles and that meet the accuracy class."""
+    """(precision, kernel shape variant) pairs that the library compiles and that meet the
+    accuracy class."""
+    base = [(MTP_FP32, 0), (MTP_FP32, 1), (MTP_FP32, 2)]
     if accuracy == "fp32":
-        return [MTP_FP32] + ([MTP_TF32X3] if dim == 3 and p <= 4 else [])
+        return base + ([(MTP_TF32X3, 0)] if dim == 3 and p <= 4 else [])
     if accuracy == "tf32":
-        return [MTP_FP32] + ([MTP_TF32X3, MTP_TF32] if dim == 3 and p <= 4 else [])
+        return base + ([(MTP_TF32X3, 0), (MTP_TF32, 0)] if dim == 3 and p <= 4 else [])
     raise ValueError("accuracy must be 'fp32' or 'tf32'")
 
 
 def autotune(dim, vertices, elements, eps, mu, p, T, lattice_values, accuracy="fp32",
              causality_factor=0.5, window=(0.1, 0.02), cache=CACHE, force=False):
-    """Return (precision, launch, record) for this workload.  ``lattice_values``: initial
+    """Return (precision, launch, record) for this workload; record["variant"] is the kernel shape
+    variant to set on the evolving tents handle (Tents.set_variant).  ``lattice_values``: initial
     lattice values (as for Mesh.state_from_lattice) used as the scratch state; ``window``:
     (start, length) of the timed layer window as fractions of the layer count."""
     import torch
@@ -78,18 +86,19 @@ def autotune(dim, vertices, elements, eps, mu, p, T, lattice_values, accuracy="f
         return rec["precision"], rec["launch"], rec
     results = []
     vals = torch.as_tensor(np.ascontiguousarray(lattice_values), device="cuda")
-    for prec in candidates(dim, p, accuracy):
+    for prec, variant in candidates(dim, p, accuracy):
         m = Mesh(dim, vertices, elements, eps, mu, p=p, precision=prec, n_rhs=vals.shape[0])
         t = m.pitch(T, causality_factor)
+        t.set_variant(variant)
         nl = t.info["n_layers"]
         lb = min(nl - 1, int(window[0] * nl))
         le = min(nl, max(lb + 1, lb + int(window[1] * nl)))
         st = m.state_from_lattice(vals)
         best, ms = t.autotune(st, lb, le)
-        results.append({"precision": prec, "launch": best, "ms": ms[best], "launch_ms": ms})
+        results.append({"precision": prec, "variant": variant, "launch": best, "ms": ms[best], "launch_ms": ms})
     top = min(results, key=lambda r: r["ms"])
-    rec = {"precision": top["precision"], "launch": top["launch"], "launch_name": LAUNCH_NAMES[top["launch"]],
-           "candidates": results}
+    rec = {"precision": top["precision"], "variant": top["variant"], "launch": top["launch"],
+           "launch_name": LAUNCH_NAMES[top["launch"]], "candidates": results}
     data[key] = rec
     _save(cache, data)
     return rec["precision"], rec["launch"], rec
