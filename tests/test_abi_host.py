@@ -133,3 +133,45 @@ def test_reference_tables_build_for_every_degree(dim):
         m = mtp.Mesh(dim, v, e, one, one, p=p)
         nb = (p + 1) * (p + 2) // 2 if dim == 2 else (p + 1) * (p + 2) * (p + 3) // 6
         assert m.info["n_basis"] == nb
+
+
+def test_kernel_variant_and_rk4_flag_validation():
+    """Host-side checks of mtp_tents_set_variant and MTP_FLAG_SUBSTITUTED_RK4 (no GPU needed)."""
+    v, e = S.cube_mesh(1)
+    one = np.ones(len(e))
+    t32 = mtp.Mesh(3, v, e, one, one, p=2, precision=mtp.MTP_FP32).pitch(0.1)
+    for variant in (0, 1, 2, 0):
+        t32.set_variant(variant)
+    for bad in (-1, 3):
+        with pytest.raises(mtp.MtpError) as ex:
+            t32.set_variant(bad)
+        assert ex.value.code == mtp.MTP_EINVAL
+    for prec in (mtp.MTP_FP64, mtp.MTP_FP32_SPLIT, mtp.MTP_TF32):
+        t = mtp.Mesh(3, v, e, one, one, p=2, precision=prec).pitch(0.1)
+        t.set_variant(0)
+        with pytest.raises(mtp.MtpError) as ex:
+            t.set_variant(1)
+        assert ex.value.code == mtp.MTP_EUNSUPPORTED
+    # the substituted-RK4 control is built in FP64 only, and only the SAT kernels take variants
+    rk = mtp.Mesh(3, v, e, one, one, p=2, precision=mtp.MTP_FP64, flags=mtp.MTP_FLAG_SUBSTITUTED_RK4)
+    with pytest.raises(mtp.MtpError) as ex:
+        rk.pitch(0.1).set_variant(2)
+    assert ex.value.code == mtp.MTP_EUNSUPPORTED
+    with pytest.raises(mtp.MtpError) as ex:
+        mtp.Mesh(3, v, e, one, one, p=2, precision=mtp.MTP_FP32, flags=mtp.MTP_FLAG_SUBSTITUTED_RK4)
+    assert ex.value.code == mtp.MTP_EUNSUPPORTED
+    with pytest.raises(mtp.MtpError) as ex:
+        mtp.Mesh(3, v, e, one, one, p=2, flags=8)
+    assert ex.value.code == mtp.MTP_EINVAL
+
+
+def test_tuner_cache_key_separates_workload_shapes():
+    from paper_1906_11029_gb300 import tune
+    a = tune._key(3, 4, "fp32", 24, 196608, 892.0)
+    assert a != tune._key(3, 4, "fp32", 24, 3072, 892.0)          # element count
+    assert a != tune._key(3, 4, "fp32", 24, 196608, 40.0)         # tents-per-layer bucket
+    assert a == tune._key(3, 4, "fp32", 24, 196608, 900.0)        # same power-of-two bucket
+    assert {c for c in tune.candidates(3, 4, "fp32")} == {
+        (mtp.MTP_FP32, 0), (mtp.MTP_FP32, 1), (mtp.MTP_FP32, 2), (mtp.MTP_TF32X3, 0)}
+    assert (mtp.MTP_TF32, 0) in tune.candidates(3, 4, "tf32")
+    assert all(c[0] == mtp.MTP_FP32 for c in tune.candidates(2, 3, "fp32"))
