@@ -463,6 +463,20 @@ def run_rk4_study(args):
             print(json.dumps(rows[-1]), flush=True)
 
 
+def run_autotune(args):
+    """Run the autotuner (paper_1906_11029_gb300/tune.py) on the workload's own initial data with a
+    fresh cache and print its record: every (precision, kernel shape variant) candidate with the
+    milliseconds of each launch configuration on the timed window of layers."""
+    import paper_1906_11029_gb300.tune as tune
+    w = make_workload(args.workload)
+    cache = os.path.join(tempfile.mkdtemp(), "tune.json")
+    prec, launch, rec = tune.autotune(w.dim, w.verts, w.elems, w.eps, w.mu, w.p, w.T, initial_lattice(w)[None],
+                                      accuracy="fp32", causality_factor=w.causality, cache=cache)
+    print(json.dumps({"workload": w.name, "choice": {"precision": prec, "variant": rec["variant"], "launch": launch,
+                                                     "launch_name": rec["launch_name"]},
+                      "candidates": rec["candidates"]}))
+
+
 def max_over_ranks(ms, dist, device):
     """The slowest rank's time (every rank gets it); `dist` None for one process."""
     import torch
@@ -677,6 +691,7 @@ def main():
     ap.add_argument("--equal-error-fp64", action="store_true",
                     help="with --equal-error: also one full FP64 p=4 evolve (about 10 min on the graded workload)")
     ap.add_argument("--rk4-study", action="store_true", help="SAT vs substituted RK4 convergence table (2D, FP64)")
+    ap.add_argument("--autotune", action="store_true", help="run the autotuner on the workload and print its record")
     ap.add_argument("--seed", type=int, default=7)
     args = ap.parse_args()
     if args.cpu_worker:
@@ -693,6 +708,8 @@ def main():
         return run_equal_error(args)
     if args.rk4_study:
         return run_rk4_study(args)
+    if args.autotune:
+        return run_autotune(args)
     return run_mtp(args)
 
 
