@@ -174,8 +174,13 @@ int mtp_tents_set_launch(mtp_tents_t tents, int launch);
  * items at half the work each, so a tent finishes sooner when the layers hold fewer tents than
  * the GPU has CTA slots (e.g. small meshes), at a lower throughput when they hold more;
  * 2 each item covers one element and one basis function (or facet mode), with 512 threads per
- * CTA in 3D: the shortest tents for such latency-bound layers.  Results are identical up to
- * rounding order.  MTP_EUNSUPPORTED for variants 1 and 2 on other meshes. */
+ * CTA in 3D: the shortest tents for such latency-bound layers.  3 and 4 (3D, p = 2..4, patches
+ * of at most 42 tetrahedra): the item shapes of 1 and 2 on 512 threads, with the volume term of
+ * the operator (Sec. 3, the element integrals of the DG semi-discretisation) computed on the
+ * tcgen05 tensor cores as TF32 MMAs with a three-term hi + lo operand split and FP32
+ * accumulation in tensor memory (FP32-level accuracy).  Results are identical up to rounding
+ * order (variants 3 and 4: up to the split's rounding).  MTP_EINVAL for a number outside 0..4,
+ * MTP_EUNSUPPORTED for variants 1..4 on meshes they are not built for. */
 int mtp_tents_set_variant(mtp_tents_t tents, int variant);
 
 /* Autotuner: times the three launch configurations on layers [layer_begin, layer_end) of

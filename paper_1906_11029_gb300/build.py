@@ -24,7 +24,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CXX_SOURCES = ["mtp_host.cpp", "mtp_tables.cpp"]
-CU_SOURCES = ["mtp_cuda.cu", "mtp_k64.cu", "mtp_k32.cu", "mtp_ks.cu", "mtp_krk.cu", "mtp_kv.cu", "mtp_kv2.cu", "mtp_ktc.cu", "mtp_kb.cu", "mtp_adj.cu", "mtp_probe.cu", "mtp_noalloc.cu", "mtp_pitch.cu"]
+CU_SOURCES = ["mtp_cuda.cu", "mtp_k64.cu", "mtp_k32.cu", "mtp_ks.cu", "mtp_krk.cu", "mtp_kv.cu", "mtp_kv2.cu", "mtp_ktc5.cu", "mtp_ktc.cu", "mtp_kb.cu", "mtp_adj.cu", "mtp_probe.cu", "mtp_noalloc.cu", "mtp_pitch.cu"]
 HEADERS = ["mtp_internal.h", "mtp_kernels.cuh", "mtp_adjoint.cuh", "mtp_launch.cuh", "../../include/mtp.h"]
 
 

@@ -47,6 +47,7 @@ struct DeviceMesh {
     float* Sf_lo = nullptr;
     float* Lfr_lo = nullptr;
     float* Trf_lo = nullptr;
+    float* Dtc = nullptr;         // tcgen05 B operand (variants 3, 4): D^T in core-matrix layout, hi then lo
     double* partial = nullptr;    // energy reduction scratch: [n_rhs][kEnergyBlocks] partials, then [n_rhs] sums
 };
 
@@ -193,6 +194,24 @@ int device_mesh_upload(Mesh& m) {
         MTP_TRY(upload_real(m, &d.Dc, thread_major(Dt, m.dim, m.nb, nbm, w, ap)));
         MTP_TRY(upload_real(m, &d.Trc, thread_major(m.ref.Tr, nv, m.nfb, m.nb, w, ap)));
         MTP_TRY(upload_real(m, &d.Lc, thread_major(m.ref.L, nv * nv, m.nb, m.nfb, w, ap)));
+        if (m.precision == MTP_FP32 && m.dim == 3 && m.p >= 2 && m.p <= 4) {
+            // B operand of the tcgen05 volume term: B[a][k], k = l nbm + c, = D_l^T[a][c], rows a
+            // padded to tn = 16, k to tk = 8, K-major core matrices (8 rows x 4 values), 8-row
+            // groups tk x 8 floats apart; TF32 hi part, then the TF32 remainder
+            const int tk = (3 * nbm + 7) / 8 * 8, tn = (m.nb + 15) / 16 * 16;
+            std::vector<float> bt((size_t)2 * tn * tk, 0.0f);
+            for (int a = 0; a < m.nb; ++a)
+                for (int l = 0; l < 3; ++l)
+                    for (int c = 0; c < nbm; ++c) {
+                        const int k = l * nbm + c;
+                        const size_t o = (size_t)(a >> 3) * tk * 8 + (k >> 2) * 32 + (a & 7) * 4 + (k & 3);
+                        const double v = Dt[((size_t)l * m.nb + a) * nbm + c];
+                        const float h = tf32_round((float)v);
+                        bt[o] = h;
+                        bt[(size_t)tn * tk + o] = tf32_round((float)(v - (double)h));
+                    }
+            MTP_TRY(upload(&d.Dtc, bt.data(), bt.size()));
+        }
         if (m.precision == MTP_FP32) {
             MTP_TRY(upload_real(m, &d.Mc1, thread_major(m.ref.M, nv, nbm, m.nb, w, 1)));
             MTP_TRY(upload_real(m, &d.Dc1, thread_major(Dt, m.dim, m.nb, nbm, w, 1)));
@@ -237,7 +256,7 @@ void device_mesh_free(Mesh& m) {
     DeviceMesh& d = *m.dev;
     void* ptrs[] = {d.geo, d.elems, d.patch_ptr, d.patch_elem, d.patch_info, d.S, d.Tr, d.L, d.Mc, d.Dc, d.Trc, d.Lc, d.Mc1, d.Dc1, d.Trc1, d.Lc1,
                     d.V, d.Vinv, d.partial,
-                    d.Sf, d.Lfr, d.Trf, d.Sf_lo, d.Lfr_lo, d.Trf_lo};
+                    d.Sf, d.Lfr, d.Trf, d.Sf_lo, d.Lfr_lo, d.Trf_lo, d.Dtc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete m.dev;
@@ -291,9 +310,10 @@ static int device_tents_upload(Tents& t) {
 }
 
 static const KernelEntry& kernel_entry(const Mesh& m, int variant = 0) {
-    static KernelEntry f64[2][5], f32[2][5], tc[2][5], split[2][5], rk4[2][5], f32v1[2][5], f32v2[2][5];
+    static KernelEntry f64[2][5], f32[2][5], tc[2][5], split[2][5], rk4[2][5], f32v1[2][5], f32v2[2][5], tc5[2][5];
     static bool init = false;
     if (!init) {
+        kernel_table_f32_tc5(tc5);
         kernel_table_f64(f64);
         kernel_table_f32(f32);
         kernel_table_tc(tc);
@@ -303,6 +323,8 @@ static const KernelEntry& kernel_entry(const Mesh& m, int variant = 0) {
         kernel_table_f32_v2(f32v2);
         init = true;
     }
+    if ((variant == 3 || variant == 4) && m.precision == MTP_FP32 && m.dim == 3 && !(m.flags & MTP_FLAG_SUBSTITUTED_RK4))
+        return tc5[variant - 3][m.p - 1];   // null entries outside p = 2..4 (refused when the variant is set)
     if (variant == 2 && m.precision == MTP_FP32 && !(m.flags & MTP_FLAG_SUBSTITUTED_RK4))
         return f32v2[m.dim - 2][m.p - 1];
     if (variant == 1 && m.precision == MTP_FP32 && !(m.flags & MTP_FLAG_SUBSTITUTED_RK4))
@@ -473,7 +495,7 @@ static void fill_args(Tents& t, void* state, KArgs& a) {
     a.Dc = dm.Dc;
     a.Trc = dm.Trc;
     a.Lc = dm.Lc;
-    if (t.variant == 2) {   // one row per thread: tables laid out with one row group per matrix row
+    if (t.variant == 2 || t.variant == 4) {   // one row per thread: one row group per matrix row
         a.Mc = dm.Mc1;
         a.Dc = dm.Dc1;
         a.Trc = dm.Trc1;
@@ -485,6 +507,7 @@ static void fill_args(Tents& t, void* state, KArgs& a) {
     a.Sf_lo = (const float4*)dm.Sf_lo;
     a.Lfr_lo = (const float4*)dm.Lfr_lo;
     a.Trf_lo = (const float4*)dm.Trf_lo;
+    a.Dtc = dm.Dtc;
     a.state = state;
     a.rhs_stride = m.ne * m.nf * m.nb;
     a.err = dt.err;

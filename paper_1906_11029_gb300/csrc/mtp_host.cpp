@@ -629,10 +629,14 @@ int mtp_tents_set_launch(mtp_tents_t tents, int launch) {
 
 int mtp_tents_set_variant(mtp_tents_t tents, int variant) {
     if (!tents) return set_error(MTP_EINVAL, "tents is NULL");
-    if (variant < 0 || variant > 2) return set_error(MTP_EINVAL, "variant must be 0, 1 or 2");
+    if (variant < 0 || variant > 4) return set_error(MTP_EINVAL, "variant must be 0 .. 4");
     const Mesh& m = *tents->t.mesh;
     if (variant > 0 && (m.precision != MTP_FP32 || (m.flags & MTP_FLAG_SUBSTITUTED_RK4)))
-        return set_error(MTP_EUNSUPPORTED, "kernel variants 1 and 2 are built for MTP_FP32 SAT meshes");
+        return set_error(MTP_EUNSUPPORTED, "kernel variants 1 .. 4 are built for MTP_FP32 SAT meshes");
+    if (variant >= 3 && (m.dim != 3 || m.p < 2 || m.p > 4))
+        return set_error(MTP_EUNSUPPORTED, "kernel variants 3 and 4 (tcgen05 volume term) are built for 3D, p = 2..4");
+    if (variant >= 3 && m.max_patch * m.nf > 256)
+        return set_error(MTP_EUNSUPPORTED, "kernel variants 3 and 4 take patches of at most 42 tetrahedra");
     tents->t.variant = variant;
     return MTP_OK;
 }

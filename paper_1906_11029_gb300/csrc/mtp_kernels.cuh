@@ -64,6 +64,9 @@ struct KArgs {
     const float4* Sf_lo;
     const float4* Lfr_lo;
     const float4* Trf_lo;
+    // tcgen05 volume operator (shapes v = 3, 4): B operand D^T[a][(l, c)] in the K-major core-
+    // matrix layout, TF32 hi part then lo part, each TN x TK floats
+    const float* Dtc;
     void* state;                // [rhs][ne][nf][nb]
     int64_t rhs_stride;         // ne * nf * nb
     int* err;                   // error word (0 = ok, 1 = causality, 2 = non-finite)
@@ -91,11 +94,15 @@ __host__ __device__ constexpr int degree_of(int dim, int r) {
 // slots (3D, 512 threads per CTA from p = 4 so that a 24-element patch still fits one round);
 // v = 2: one element and one basis function (or facet mode) per item, 512 threads per CTA in
 // 3D: every phase of a 24-element p <= 3 patch in one round at a quarter of the default's
-// per-thread work, for the shortest tents on latency-bound layers.
+// per-thread work, for the shortest tents on latency-bound layers.  v = 3, 4: the item shapes
+// of v = 1, 2 (512 threads) with the volume term on the tcgen05 tensor cores (3D FP32, see
+// the tcgen05 section at the end of this file).
 template <int DIM, int PV>
 struct Shape {
     static constexpr int P = PV & 15, V = PV >> 4;
-    static constexpr bool PAIRS = V == 0;                 // FP32 items pair elements (FP64 never)
+    static constexpr bool TC5 = V >= 3;                   // volume term on tcgen05
+    static constexpr int VB = V == 3 ? 1 : V == 4 ? 2 : V;   // item shape
+    static constexpr bool PAIRS = VB == 0;                // FP32 items pair elements (FP64 never)
     static constexpr int NF = DIM == 2 ? 3 : 6;
     static constexpr int NB = DIM == 2 ? (P + 1) * (P + 2) / 2 : (P + 1) * (P + 2) * (P + 3) / 6;
     static constexpr int NFB = DIM == 2 ? P + 1 : (P + 1) * (P + 2) / 2;
@@ -103,8 +110,8 @@ struct Shape {
     static constexpr int NFBP = pad4(NFB);
     static constexpr int GIS = pad4(NF);                  // row stride of G^-1 in shared memory
     static constexpr int NV = DIM + 1;
-    static constexpr int NT = DIM == 2 ? 128 : ((V == 1 && P >= 4) || V == 2 ? 512 : 256);   // threads per CTA
-    static constexpr int AP = V == 2 ? 1 : 2;          // basis functions (facet modes) per thread
+    static constexpr int NT = DIM == 2 ? 128 : ((VB == 1 && (P >= 4 || TC5)) || VB == 2 ? 512 : 256);   // threads per CTA
+    static constexpr int AP = VB == 2 ? 1 : 2;         // basis functions (facet modes) per thread
     static constexpr int NAG = (NB + AP - 1) / AP;     // basis groups per element
     static constexpr int NCG = (NFB + AP - 1) / AP;    // facet-mode groups per facet
     // Degree structure of the tables (basis ordered by degree): S[a][b] = 0 for deg b > deg a
@@ -129,6 +136,14 @@ struct Shape {
     static constexpr int BW1 = dim_pk(DIM, DC1 + 1);
     static constexpr int DC2 = degree_of(DIM, NWG);
     static constexpr int BW2 = dim_pk(DIM, DC2 - 2);
+    // tcgen05 volume operator: K = (direction l, row c < NBM) padded to the MMA's k = 8, N = basis
+    // functions a padded to 16, the accumulators of two 128-row chunks in TCOLS TMEM columns; the
+    // volume result goes to shared memory with the odd row stride VS (conflict-free banks)
+    static constexpr int TK = (DIM * NBM + 7) / 8 * 8;
+    static constexpr int TN = (NB + 15) / 16 * 16;
+    static constexpr int TCOLS = 2 * TN <= 32 ? 32 : 2 * TN <= 64 ? 64 : 2 * TN <= 128 ? 128 : 256;
+    static constexpr int VS = NB % 2 ? NB : NB + 1;
+    static_assert(!TC5 || (DIM == 3 && VS <= TK && 2 * TN <= TCOLS), "tcgen05 volume layout");
 };
 
 // CTAs per SM the register budget is shaped for (two 256-thread CTAs fit the FP32 3D
@@ -190,13 +205,15 @@ struct SmemLayout {
     static __host__ __device__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
     size_t off_Y, off_Ylo, off_Ua, off_Ub, off_W, off_tr, off_Gi, off_gphi, off_gdel, off_mat, off_ac, off_gd,
         off_nrm, off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, off_pair, off_own, bytes, state_bytes, tr_bytes;
+    size_t off_tA, off_tB, off_tbar;   // tcgen05 operands (hi, lo parts), mbarriers + TMEM address
+    int tc_rows;                       // A-operand rows: 128-row chunks cover (element, field) rows
     bool split, factored, twobuf, rk4;   // rk4: Y at the sub-step start (Ylo slot), stage input (Ub)
     // mode (see ModeTraits): split carries the Taylor accumulator Y as an unevaluated pair
     // hi + lo (one more patch-state buffer); the SIMT modes use the factored volume term (a W
     // buffer) and update U in place, the tensor-core modes keep two U buffers (twobuf also
     // asks for the second one, for the adjoint's reverse recursion)
     __host__ __device__ explicit SmemLayout(int mp, int mode = 0, bool two = false)
-        : split(mode == 3), factored(mode == 0 || mode == 3 || mode == 4),
+        : split(mode == 3), factored((mode == 0 || mode == 3 || mode == 4) && !Sh::TC5),
           twobuf(two || mode == 1 || mode == 2 || mode == 4), rk4(mode == 4) {
         size_t o = 0;
         state_bytes = (size_t)mp * Sh::NF * Sh::NBP * sizeof(Real);
@@ -222,6 +239,15 @@ struct SmemLayout {
         off_nfi = o; o = align16(o + (size_t)mp * DIM);
         off_pair = o; o = align16(o + (size_t)mp * 2 + 4);
         off_own = o; o = align16(o + (size_t)mp * DIM * 2 + 4);
+        tc_rows = 0;
+        off_tA = off_tB = off_tbar = o;
+        if (Sh::TC5) {
+            const int r = (mp * Sh::NF + 7) / 8 * 8;
+            tc_rows = r < 128 ? 128 : r;
+            off_tA = o = (o + 127) & ~size_t(127); o += (size_t)2 * tc_rows * Sh::TK * sizeof(float);
+            off_tB = o; o += (size_t)2 * Sh::TN * Sh::TK * sizeof(float);
+            off_tbar = o; o += 32;
+        }
         bytes = o;
     }
 };
@@ -273,6 +299,13 @@ struct TentCtx {
     int8_t* sOwn;                         // [facet][2]: (slot, facet position) owning each facet
     int* sNpair;
     int* sNown;
+    // tcgen05 volume operator: A operand hi / lo, B operand (D tables) hi / lo, volume result
+    // (over the A hi part once the MMAs have read it), mbarriers [MMA done, tables loaded] and
+    // [TMEM address, MMA phase, failure flag]
+    float *sAh, *sAl, *sBh, *sBl, *sVol;
+    uint64_t* sBar;
+    uint32_t* sTc;
+    int tc_rows;
     int V, ns;
     int64_t pb;
     double tb, dt;
@@ -302,8 +335,202 @@ struct TentCtx {
         sNpair = (int*)(smem + lay.off_pair);
         sOwn = (int8_t*)(smem + lay.off_own + 4);
         sNown = (int*)(smem + lay.off_own);
+        tc_rows = lay.tc_rows;
+        if (Sh::TC5) {
+            sAh = (float*)(smem + lay.off_tA);
+            sAl = sAh + (size_t)lay.tc_rows * Sh::TK;
+            sBh = (float*)(smem + lay.off_tB);
+            sBl = sBh + Sh::TN * Sh::TK;
+            sVol = sAh;
+            sBar = (uint64_t*)(smem + lay.off_tbar);
+            sTc = (uint32_t*)(smem + lay.off_tbar + 16);
+        } else {
+            sAh = sAl = sBh = sBl = sVol = nullptr;
+            sBar = nullptr;
+            sTc = nullptr;
+        }
     }
 };
+
+// ---------------------------------------------------------------------------------------
+// tcgen05 primitives (inline PTX, sm_103a) for the volume operator of kernel shapes v = 3, 4.
+// Operands live in shared memory in the no-swizzle K-major layout: 8-row x 16-byte core
+// matrices, the 4-element k groups of one 8-row group 128 B apart, 8-row groups TK x 32 B
+// apart; the accumulator of a 128-row MMA occupies TMEM lanes 0..127 (one row per lane).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t tf32_bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ long long tc_clock() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// float index of entry (row r, k) of a K-major operand with TK columns
+template <int TK>
+__device__ __forceinline__ int tc_off(int r, int k) {
+    return (r >> 3) * TK * 8 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3);
+}
+// shared-memory matrix descriptor: start address, k-group stride (LBO), 8-row-group stride
+// (SBO), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// bounded wait for the phase of `parity` of a shared-memory mbarrier (false after one second)
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    long long deadline = 0;
+    for (int it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        const long long now = tc_clock();
+        if (it == 0) deadline = now + 1000000000LL;
+        else if (now > deadline) return false;
+    }
+}
+// 16 consecutive TMEM columns of this warp's 32 lanes, one column per register
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t v[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Once per CTA before its first tent: zero the A operand (its K padding and spare rows must be
+// finite), initialise the two mbarriers, bring both parts of the D tables into shared memory with
+// one bulk asynchronous copy (the TMA engine's non-tensor form) and allocate the TMEM columns.
+template <typename Real, int DIM, int P>
+__device__ void tc5_begin(TentCtx<Real, DIM, P>& c, const KArgs& a) {
+    using Sh = Shape<DIM, P>;
+    float4* A4 = (float4*)c.sAh;
+    const int n4 = 2 * c.tc_rows * Sh::TK / 4;
+    for (int i = threadIdx.x; i < n4; i += Sh::NT) A4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (threadIdx.x == 0) {
+        c.sTc[1] = 0;
+        c.sTc[2] = a.Dtc ? 0u : 1u;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&c.sBar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&c.sBar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool have_tables = a.Dtc != nullptr;
+    if (threadIdx.x == 0 && have_tables) {
+        const uint32_t bytes = 2u * Sh::TN * Sh::TK * 4u, bar = smem_u32(&c.sBar[1]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(c.sBh)),
+                     "l"(a.Dtc), "r"(bytes), "r"(bar)
+                     : "memory");
+    }
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&c.sTc[0])),
+                     "r"(Sh::TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (!have_tables) {
+        if (threadIdx.x == 0) atomicCAS(a.err, 0, 3);
+    } else if (!tc_wait(&c.sBar[1], 0)) {
+        atomicCAS(a.err, 0, 3);
+        c.sTc[2] = 1;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// After the CTA's last tent: release the TMEM columns
+template <typename Real, int DIM, int P>
+__device__ void tc5_end(TentCtx<Real, DIM, P>& c) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c.sTc[0]), "r"(Shape<DIM, P>::TCOLS)
+                     : "memory");
+}
+
+// One thread issues the stage's volume MMAs: for each 128-row chunk of (element, field) rows
+// (the second chunk ends at the last row), D[rows][a] = sum over k of A[rows][k] B[a][k] as
+// A_lo B_hi + A_hi B_lo + A_hi B_hi, TF32 operands, FP32 accumulation in TMEM, then a commit
+// to the MMA mbarrier.
+template <typename Real, int DIM, int P>
+__device__ void tc5_issue(TentCtx<Real, DIM, P>& c) {
+    using Sh = Shape<DIM, P>;
+    constexpr uint32_t SBO = Sh::TK * 32;
+    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Sh::TN >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = c.sTc[0];
+    const int nch = c.ns * Sh::NF > 128 ? 2 : 1;
+    const uint32_t aop[2] = {smem_u32(c.sAh), smem_u32(c.sAl)}, bop[2] = {smem_u32(c.sBh), smem_u32(c.sBl)};
+    for (int ch = 0; ch < nch; ++ch) {
+        const uint32_t r0 = ch == 0 ? 0u : (uint32_t)(c.tc_rows - 128);
+        const uint32_t d = tbase + (uint32_t)(ch * Sh::TN);
+        uint32_t acc = 0;
+        for (int t = 0; t < 3; ++t) {
+            const uint32_t A = aop[t == 0 ? 1 : 0] + (r0 / 8) * SBO, B = bop[t == 1 ? 1 : 0];
+            for (int s = 0; s < Sh::TK / 8; ++s) {
+                const uint64_t ad = tc_desc(A + s * 256, 128, SBO), bd = tc_desc(B + s * 256, 128, SBO);
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                    "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
+                    : "memory");
+                acc = 1;
+            }
+        }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&c.sBar[0]))
+                 : "memory");
+}
+
+// All threads: wait (bounded) for the stage's MMAs, then the warps copy the accumulators of
+// their TMEM lane quarter to sVol[(element, field) row][a] (row stride VS) over the A operand,
+// which the finished MMAs no longer read.
+template <typename Real, int DIM, int P>
+__device__ void tc5_collect(TentCtx<Real, DIM, P>& c, const KArgs& a, uint32_t parity) {
+    using Sh = Shape<DIM, P>;
+    constexpr int NCB = Sh::TN / 16, VS = Sh::VS, NB = Sh::NB;
+    if (c.sTc[2] == 0 && !tc_wait(&c.sBar[0], parity)) {
+        atomicCAS(a.err, 0, 3);
+        c.sTc[2] = 1;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3;
+    const int rows = c.ns * Sh::NF;
+    const int nch = rows > 128 ? 2 : 1;
+    const uint32_t tbase = c.sTc[0];
+    for (int u = warp >> 2; u < nch * NCB; u += Sh::NT / 128) {
+        const int ch = u / NCB, cb = u - ch * NCB;
+        const int r0 = (ch == 0 ? 0 : c.tc_rows - 128) + 32 * q;   // row of this quarter's lane 0
+        if (r0 >= rows || (ch == 1 && r0 + 31 < 128)) continue;     // warp-uniform
+        uint32_t v[16];
+        tc_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(ch * Sh::TN + cb * 16), v);
+        const int r = r0 + lane;
+        if (r < rows && (ch == 0 || r >= 128)) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int col = cb * 16 + j;
+                if (col < NB) c.sVol[r * VS + col] = __uint_as_float(v[j]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
 
 // (a) gather: per-element setup from FP64 geometry and the current front; patch state of
 // `src` into sY (pads zero); U and facet buffers zeroed so their pads stay zero.
@@ -586,16 +813,43 @@ __device__ __forceinline__ void tent_w_item(TentCtx<Real, DIM, P>& c, const KArg
     for (int b = B2; b < B1c; b += W) block(b, I0{}, I2{});
 #pragma unroll 1
     for (int b = B1c; b < NBP; b += W) block(b, I1{}, I2{});
-#pragma unroll
-    for (int e = 0; e < EP; ++e) {
-        if (e == 1 && kk1 < 0) break;
-        Real* out = c.sW + kk[e] * WSZ;
+    if constexpr (Sh::TC5 && DIM == 3) {
+        // A operand of the tcgen05 volume term: the curl combination folded into W,
+        // A[(k, f)][(l, c)] = (E rows: -a_l x W_H, H rows: a_l x W_E)_f, so that the MMA with
+        // B[a][(l, c)] = D_l^T[a][c] gives the element's volume term directly; TF32 hi + lo
+        const Real* ac = c.sAc + k0 * DIM * 3;
 #pragma unroll
         for (int ci = 0; ci < AP; ++ci) {
             const int row = g + ci * NWG;
             if (row < NBM) {
+                const Real* w = acc[0][ci];
 #pragma unroll
-                for (int s = 0; s < NF; ++s) out[s * NBMP + row] = acc[e][ci][s];
+                for (int l = 0; l < DIM; ++l) {
+                    const Real ax = ac[3 * l], ay = ac[3 * l + 1], az = ac[3 * l + 2];
+                    const Real v[6] = {az * w[4] - ay * w[5], ax * w[5] - az * w[3], ay * w[3] - ax * w[4],
+                                       ay * w[2] - az * w[1], az * w[0] - ax * w[2], ax * w[1] - ay * w[0]};
+#pragma unroll
+                    for (int f = 0; f < 6; ++f) {
+                        const int o = tc_off<Sh::TK>(k0 * 6 + f, l * NBM + row);
+                        const float h = __uint_as_float(tf32_bits(v[f]));
+                        c.sAh[o] = h;
+                        c.sAl[o] = __uint_as_float(tf32_bits(v[f] - h));
+                    }
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < EP; ++e) {
+            if (e == 1 && kk1 < 0) break;
+            Real* out = c.sW + kk[e] * WSZ;
+#pragma unroll
+            for (int ci = 0; ci < AP; ++ci) {
+                const int row = g + ci * NWG;
+                if (row < NBM) {
+#pragma unroll
+                    for (int s = 0; s < NF; ++s) out[s * NBMP + row] = acc[e][ci][s];
+                }
             }
         }
     }
@@ -607,7 +861,7 @@ __device__ __forceinline__ void tent_w_item(TentCtx<Real, DIM, P>& c, const KArg
 // last round of trace items leaves idle
 template <typename Real, int DIM, int P>
 __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real* Ucur, Real* tr) {
-    if (c.sW) {
+    if (c.sW || Shape<DIM, P>::TC5) {   // W = M_j U, or the tcgen05 A operand built from it
         constexpr int NT = Shape<DIM, P>::NT;
         const int nitems = ((sizeof(Real) == 4 && Shape<DIM, P>::PAIRS) ? *c.sNpair : c.ns) * Shape<DIM, P>::NWG;
         const int busy = (c.ns * Shape<DIM, P>::NCG) % NT, idle = NT - busy;
@@ -754,7 +1008,13 @@ __device__ void tent_stage(TentCtx<Real, DIM, P>& c, const KArgs& a, int n, cons
         int kk[2] = {k0, has1 ? kk1 : k0};
         const int j = c.sJ[k0];
         Real Yn[EP][AP][NF];
-        {
+        if constexpr (Sh::TC5) {   // volume term from the tcgen05 accumulators
+#pragma unroll
+            for (int ai = 0; ai < AP; ++ai)
+#pragma unroll
+                for (int s = 0; s < NF; ++s)
+                    Yn[0][ai][s] = (ai == 0 || two) ? c.sVol[(k0 * NF + s) * Sh::VS + ag + ai * NAG] : Real(0);
+        } else {
             const Real* Dg = (const Real*)a.Dc + ag * W;
             Real Pm[EP][AP][DIM][NF];
 #pragma unroll
@@ -992,7 +1252,32 @@ __device__ void tent_sat(TentCtx<Real, DIM, P>& c, const KArgs& a, Real* tape) {
     }
     constexpr int ESZ = Shape<DIM, P>::NF * Shape<DIM, P>::NBP;
     const size_t slot = (size_t)a.max_patch * ESZ;
-    if constexpr (ModeTraits<MODE>::simt) {
+    if constexpr (Shape<DIM, P>::TC5) {
+        // SIMT traces (+ A operand), fluxes and epilogue; the volume MMAs run on the tensor
+        // cores while the fluxes are computed.  U is updated in place.
+        Real* U = c.sUa;
+        uint32_t ph = c.sTc[1];
+        for (int i = 0; i < a.m; ++i) {
+            tent_ginv(c, a, i);
+            __syncthreads();
+            tent_apply_ginv(c, c.sY, U);
+            __syncthreads();
+            for (int n = 1; n <= a.q; ++n) {
+                tent_traces(c, a, U, c.sTr);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // A visible to the MMAs
+                __syncthreads();
+                if (threadIdx.x == 0) tc5_issue(c);
+                tent_fluxes(c, c.sTr);
+                tc5_collect(c, a, ph);
+                ph ^= 1u;
+                __syncthreads();
+                tent_stage<Real, DIM, P, 0>(c, a, n, U, U, c.sTr);
+                __syncthreads();
+            }
+        }
+        if (threadIdx.x == 0) c.sTc[1] = ph;
+        return;
+    } else if constexpr (ModeTraits<MODE>::simt) {
         // U is updated in place: the factored stage reads only its own rows of U
         Real* U = c.sUa;
         for (int i = 0; i < a.m; ++i) {
@@ -1045,8 +1330,10 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::va
     c.carve(smem, lay);
     const int64_t tent = t0 + blockIdx.x;
     StateT* state = (StateT*)a.state + (int64_t)blockIdx.y * a.rhs_stride;
+    if constexpr (Sh::TC5) tc5_begin(c, a);
     tent_setup(c, a, tent, state);
     tent_sat<Real, DIM, P, MODE>(c, a, (Real*)nullptr);
+    if constexpr (Sh::TC5) tc5_end(c);
     // ---- (d) scatter the tent-top Y; advance the front at V ----
     bool bad = false;
     for (int idx = threadIdx.x; idx < c.ns * NF * NB; idx += NT) {
@@ -1160,6 +1447,11 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::va
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long s_ticket;
     __shared__ int s_abort;
+    TentCtx<Real, DIM, P> tc;
+    if constexpr (Shape<DIM, P>::TC5) {
+        tc.carve(smem, SmemLayout<Real, DIM, P>(a.max_patch, MODE));
+        tc5_begin(tc, a);
+    }
     while (true) {
         if (threadIdx.x == 0) {
             s_ticket = (long long)atomicAdd(pa.next, 1ull);
@@ -1170,6 +1462,7 @@ __global__ void __launch_bounds__(Shape<DIM, P>::NT, MinBlocks<Real, DIM, P>::va
         if (ticket >= pa.n_tents) break;
         if (!tent_dag_step<Real, DIM, P, MODE>(smem, a, pa, pa.ticket0 + ticket, &s_abort)) break;
     }
+    if constexpr (Shape<DIM, P>::TC5) tc5_end(tc);
 }
 
 // Many independent problems (meshes of any degree 1..5, same dimension and precision) in one

@@ -78,6 +78,8 @@ void kernel_table_rk4(KernelEntry entries[2][5]);
 // per item, 512 threads); see Shape
 void kernel_table_f32_v1(KernelEntry entries[2][5]);
 void kernel_table_f32_v2(KernelEntry entries[2][5]);
+// FP32 3D, volume term on tcgen05 (variants 3 and 4, p = 2..4): entries[variant - 3][p - 1]
+void kernel_table_f32_tc5(KernelEntry entries[2][5]);
 
 struct AdjArgs;
 using AdjLaunchFn = cudaError_t (*)(const AdjArgs&, int64_t t0, int n_tents, int n_rhs, cudaStream_t st);

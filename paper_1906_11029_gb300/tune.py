@@ -11,7 +11,8 @@ Two levels:
 * kernel shape of the SIMT FP32 kernels (here, `mtp_tents_set_variant`): stage items over pairs
   of patch elements (variant 0), single elements (variant 1) or single (element, row) pairs on
   512 threads (variant 2): more and shorter items, faster tents when the layers hold fewer
-  tents than the GPU has CTA slots.
+  tents than the GPU has CTA slots; variants 3 and 4 (3D, p = 2..4) take the item shapes of 1
+  and 2 with the volume term on the tcgen05 tensor cores.
 Candidates are timed on the same layer window of the caller's workload.
 
 Choices are cached in a JSON file (default ``~/.cache/paper_1906_11029_gb300/tune.json``)
@@ -27,7 +28,7 @@ import os
 
 import numpy as np
 
-from . import MTP_FP32, MTP_TF32, MTP_TF32X3, Mesh
+from . import MTP_EUNSUPPORTED, MTP_FP32, MTP_TF32, MTP_TF32X3, Mesh, MtpError
 
 CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1906_11029_gb300", "tune.json")
 LAUNCH_NAMES = ["dag_walk", "dag_walk_1cta", "layer_launches"]
@@ -62,6 +63,8 @@ def candidates(dim, p, accuracy):
     """(precision, kernel shape variant) pairs that the library compiles and that meet the
     accuracy class."""
     base = [(MTP_FP32, 0), (MTP_FP32, 1), (MTP_FP32, 2)]
+    if dim == 3 and 2 <= p <= 4:
+        base += [(MTP_FP32, 3), (MTP_FP32, 4)]   # volume term on tcgen05 (3xTF32, FP32 accuracy)
     if accuracy == "fp32":
         return base + ([(MTP_TF32X3, 0)] if dim == 3 and p <= 4 else [])
     if accuracy == "tf32":
@@ -89,7 +92,12 @@ def autotune(dim, vertices, elements, eps, mu, p, T, lattice_values, accuracy="f
     for prec, variant in candidates(dim, p, accuracy):
         m = Mesh(dim, vertices, elements, eps, mu, p=p, precision=prec, n_rhs=vals.shape[0])
         t = m.pitch(T, causality_factor)
-        t.set_variant(variant)
+        try:
+            t.set_variant(variant)
+        except MtpError as e:   # e.g. a patch too large for the tcgen05 variants
+            if e.code != MTP_EUNSUPPORTED:
+                raise
+            continue
         nl = t.info["n_layers"]
         lb = min(nl - 1, int(window[0] * nl))
         le = min(nl, max(lb + 1, lb + int(window[1] * nl)))

@@ -140,12 +140,22 @@ def test_kernel_variant_and_rk4_flag_validation():
     v, e = S.cube_mesh(1)
     one = np.ones(len(e))
     t32 = mtp.Mesh(3, v, e, one, one, p=2, precision=mtp.MTP_FP32).pitch(0.1)
-    for variant in (0, 1, 2, 0):
+    for variant in (0, 1, 2, 3, 4, 0):
         t32.set_variant(variant)
-    for bad in (-1, 3):
+    for bad in (-1, 5):
         with pytest.raises(mtp.MtpError) as ex:
             t32.set_variant(bad)
         assert ex.value.code == mtp.MTP_EINVAL
+    # the tcgen05 variants are built for 3D, p = 2..4
+    vs, es = S.square_mesh(2)
+    cases = [(2, vs, es, 2), (3, v, e, 1), (3, v, e, 5)]
+    for dim, vv, ee, p in cases:
+        t = mtp.Mesh(dim, vv, ee, np.ones(len(ee)), np.ones(len(ee)), p=p, precision=mtp.MTP_FP32).pitch(0.1)
+        t.set_variant(2)
+        for tcv in (3, 4):
+            with pytest.raises(mtp.MtpError) as ex:
+                t.set_variant(tcv)
+            assert ex.value.code == mtp.MTP_EUNSUPPORTED, (dim, p, tcv)
     for prec in (mtp.MTP_FP64, mtp.MTP_FP32_SPLIT, mtp.MTP_TF32):
         t = mtp.Mesh(3, v, e, one, one, p=2, precision=prec).pitch(0.1)
         t.set_variant(0)
@@ -172,6 +182,8 @@ def test_tuner_cache_key_separates_workload_shapes():
     assert a != tune._key(3, 4, "fp32", 24, 196608, 40.0)         # tents-per-layer bucket
     assert a == tune._key(3, 4, "fp32", 24, 196608, 900.0)        # same power-of-two bucket
     assert {c for c in tune.candidates(3, 4, "fp32")} == {
-        (mtp.MTP_FP32, 0), (mtp.MTP_FP32, 1), (mtp.MTP_FP32, 2), (mtp.MTP_TF32X3, 0)}
+        (mtp.MTP_FP32, 0), (mtp.MTP_FP32, 1), (mtp.MTP_FP32, 2), (mtp.MTP_FP32, 3), (mtp.MTP_FP32, 4),
+        (mtp.MTP_TF32X3, 0)}
+    assert (mtp.MTP_FP32, 3) not in tune.candidates(3, 5, "fp32")
     assert (mtp.MTP_TF32, 0) in tune.candidates(3, 4, "tf32")
     assert all(c[0] == mtp.MTP_FP32 for c in tune.candidates(2, 3, "fp32"))

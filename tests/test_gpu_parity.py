@@ -140,11 +140,12 @@ def _oracle_tents_prefix(w, gpu_tents, n_layers):
     return ot
 
 
-def _single_layer_check(w, precision, layer_frac, n_sample, seed):
+def _single_layer_check(w, precision, layer_frac, n_sample, seed, variant=0):
     """Full-size workload, the launch configuration of a real evolve: one layer applied to a
     seeded random state on the GPU; the oracle recomputes a sample of that layer's tents."""
     m = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=precision)
     t = m.pitch(w.T, w.causality)
+    t.set_variant(variant)
     gpu_tents = t.get()
     L = int(layer_frac * (len(gpu_tents["layer_ptr"]) - 1))
     tents = _oracle_tents_prefix(w, gpu_tents, L + 1)
@@ -177,23 +178,27 @@ def test_cube16_p3_single_layer_sampled(precision):
     assert err <= TOL[precision], err
 
 
-@pytest.mark.parametrize("precision", [mtp.MTP_FP64, mtp.MTP_FP32])
-def test_graded32_p4_single_layer_sampled(precision):
-    """Graded 32^3 x 6 tets, p = 4, eps = 4 ball (full size of the mixed-precision workload)."""
+@pytest.mark.parametrize("precision,variant", [(mtp.MTP_FP64, 0), (mtp.MTP_FP32, 0), (mtp.MTP_FP32, 3)])
+def test_graded32_p4_single_layer_sampled(precision, variant):
+    """Graded 32^3 x 6 tets, p = 4, eps = 4 ball (full size of the mixed-precision workload);
+    variant 3 computes the volume term on the tcgen05 tensor cores."""
     w = S.graded_sphere(32, 4, 0.5)
-    err = _single_layer_check(w, precision, 0.3, 3, 202)
+    err = _single_layer_check(w, precision, 0.3, 3, 202, variant)
     assert err <= TOL[precision], err
 
 
-@pytest.mark.parametrize("precision", [mtp.MTP_FP64, mtp.MTP_FP32, mtp.MTP_FP32_SPLIT])
-def test_cube16_p3_twenty_layers_dag_walk(precision):
+@pytest.mark.parametrize("precision,variant", [(mtp.MTP_FP64, 0), (mtp.MTP_FP32, 0), (mtp.MTP_FP32_SPLIT, 0),
+                                               (mtp.MTP_FP32, 3), (mtp.MTP_FP32, 4)])
+def test_cube16_p3_twenty_layers_dag_walk(precision, variant):
     """3D cavity workload at full size (16^3 x 6 perturbed tets, p = 3, T = 1): 20 consecutive
     layers from the middle of the evolve applied by the persistent DAG walk (one launch, the
     bench's launch configuration) to a seeded random state; the oracle applies every tent of
-    the same 20 layers.  Compared on every element the layers touch."""
+    the same 20 layers.  Compared on every element the layers touch.  Variants 3 and 4 run the
+    volume term on the tcgen05 tensor cores."""
     w = S.cube_mode(16, 3, 1.0)
     m = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=3, precision=precision)
     t = m.pitch(w.T, w.causality)
+    t.set_variant(variant)
     tents = t.get()
     L0 = (len(tents["layer_ptr"]) - 1) // 2
     L1 = L0 + 20

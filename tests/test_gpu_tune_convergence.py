@@ -56,10 +56,11 @@ def test_autotuner_picks_and_caches(tmp_path):
                                       accuracy="fp32", cache=cache)
     assert prec in (mtp.MTP_FP32, mtp.MTP_TF32X3) and launch in (0, 1, 2)
     assert os.path.exists(cache)
-    assert len(rec["candidates"]) == 4 and all(len(c["launch_ms"]) == 3 for c in rec["candidates"])
-    assert rec["variant"] in (0, 1, 2)
+    assert len(rec["candidates"]) == 6 and all(len(c["launch_ms"]) == 3 for c in rec["candidates"])
+    assert rec["variant"] in (0, 1, 2, 3, 4)
     assert {(c["precision"], c["variant"]) for c in rec["candidates"]} == {
-        (mtp.MTP_FP32, 0), (mtp.MTP_FP32, 1), (mtp.MTP_FP32, 2), (mtp.MTP_TF32X3, 0)}
+        (mtp.MTP_FP32, 0), (mtp.MTP_FP32, 1), (mtp.MTP_FP32, 2), (mtp.MTP_FP32, 3), (mtp.MTP_FP32, 4),
+        (mtp.MTP_TF32X3, 0)}
     again = tune.autotune(3, w.verts, w.elems, w.eps, w.mu, w.p, w.T, _vals(w), accuracy="fp32", cache=cache)
     assert again[0] == prec and again[1] == launch
 

@@ -1,6 +1,7 @@
 """Kernel shape variants 1 (one patch element per stage item) and 2 (one element and one row per
-item, 512 threads) selected with mtp_tents_set_variant, against the default paired variant and
-against the oracle, FP32."""
+item, 512 threads), and 3, 4 (those item shapes with the volume term on the tcgen05 tensor
+cores, 3xTF32 with FP32 accumulation in tensor memory) selected with mtp_tents_set_variant,
+against the default paired variant and against the oracle, FP32."""
 import numpy as np
 import pytest
 
@@ -43,14 +44,41 @@ def test_variants_match_oracle_and_variant0(name):
             assert rel_l2(v1, v0) <= 2e-6
 
 
+_TC5_CASES = {
+    "cube_n2_p2": lambda: S.cube_mode(2, 2, 0.12),
+    "cube_n2_p3": lambda: S.cube_mode(2, 3, 0.1),
+    "cube_n2_p4": lambda: S.cube_mode(2, 4, 0.04),
+    "graded_n3_p2": lambda: S.graded_sphere(n=3, p=2, T=0.06, width=0.3),   # eps jump: impedances differ
+    "graded_n3_p4": lambda: S.graded_sphere(n=3, p=4, T=0.03, width=0.3),
+}
+
+
+@pytest.mark.parametrize("name", list(_TC5_CASES))
+def test_tcgen05_variants_match_oracle_and_variant0(name):
+    """Patches from 1 to 24 tetrahedra: up to 128 (element, field) rows take one MMA chunk, the
+    24-tet interior patches (144 rows) two.  Both the persistent DAG walk and per-layer
+    launches (each CTA allocates and frees its own tensor memory)."""
+    w = _TC5_CASES[name]()
+    vals0, ref, _, _ = oracle_full_run(w)
+    v0 = _run(w, vals0, 0)
+    for variant in (3, 4):
+        for launch in (0, 2):
+            v1 = _run(w, vals0, variant, launch)
+            err, emax = rel_l2(v1, ref), max_rel(v1, ref)
+            print(f"{name} variant {variant} launch {launch}: rel l2 {err:.2e}, element-wise max {emax:.2e}, "
+                  f"vs variant 0 {rel_l2(v1, v0):.2e}")
+            assert err <= 1e-5 and emax <= 1e-5, (err, emax)
+            assert rel_l2(v1, v0) <= 5e-6
+
+
 def test_variants_refused_outside_fp32():
     w = S.cube_mode(2, 2, 0.1)
     m = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=2, precision=mtp.MTP_FP64)
     t = m.pitch(w.T)
-    for v in (1, 2):
+    for v in (1, 2, 3, 4):
         with pytest.raises(mtp.MtpError) as ex:
             t.set_variant(v)
         assert ex.value.code == mtp.MTP_EUNSUPPORTED
     with pytest.raises(mtp.MtpError) as ex:
-        t.set_variant(3)
+        t.set_variant(5)
     assert ex.value.code == mtp.MTP_EINVAL
