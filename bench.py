@@ -268,6 +268,7 @@ def run_profile(args):
     flags = mtp.MTP_FLAG_LAYER_LAUNCHES if args.layer_launches else 0
     mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=w.p, precision=prec, flags=flags)
     tents = mesh.pitch(w.T, w.causality)
+    tents.set_variant(args.variant)
     state = mesh.state_from_lattice(torch.tensor(initial_lattice(w)[None], device="cuda"))
     if a > 0:
         tents.evolve_layers(state, 0, a)

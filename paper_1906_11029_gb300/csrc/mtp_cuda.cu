@@ -47,7 +47,7 @@ struct DeviceMesh {
     float* Sf_lo = nullptr;
     float* Lfr_lo = nullptr;
     float* Trf_lo = nullptr;
-    float* Dtc = nullptr;         // tcgen05 B operand (variants 3, 4): D^T in core-matrix layout, hi then lo
+    float* Dtc = nullptr;         // tcgen05 A operand (variants 3, 4): D^T in core-matrix layout, hi then lo
     double* partial = nullptr;    // energy reduction scratch: [n_rhs][kEnergyBlocks] partials, then [n_rhs] sums
 };
 
@@ -195,10 +195,10 @@ int device_mesh_upload(Mesh& m) {
         MTP_TRY(upload_real(m, &d.Trc, thread_major(m.ref.Tr, nv, m.nfb, m.nb, w, ap)));
         MTP_TRY(upload_real(m, &d.Lc, thread_major(m.ref.L, nv * nv, m.nb, m.nfb, w, ap)));
         if (m.precision == MTP_FP32 && m.dim == 3 && m.p >= 2 && m.p <= 4) {
-            // B operand of the tcgen05 volume term: B[a][k], k = l nbm + c, = D_l^T[a][c], rows a
-            // padded to tn = 16, k to tk = 8, K-major core matrices (8 rows x 4 values), 8-row
-            // groups tk x 8 floats apart; TF32 hi part, then the TF32 remainder
-            const int tk = (3 * nbm + 7) / 8 * 8, tn = (m.nb + 15) / 16 * 16;
+            // A operand of the tcgen05 volume term: D[a][k], k = l nbm + c, = D_l^T[a][c], rows a
+            // padded to tn = 64 (the MMA's M), k to tk = 8, K-major core matrices (8 rows x 4
+            // values), 8-row groups tk x 8 floats apart; TF32 hi part, then the TF32 remainder
+            const int tk = (3 * nbm + 7) / 8 * 8, tn = 64;
             std::vector<float> bt((size_t)2 * tn * tk, 0.0f);
             for (int a = 0; a < m.nb; ++a)
                 for (int l = 0; l < 3; ++l)

@@ -64,8 +64,8 @@ struct KArgs {
     const float4* Sf_lo;
     const float4* Lfr_lo;
     const float4* Trf_lo;
-    // tcgen05 volume operator (shapes v = 3, 4): B operand D^T[a][(l, c)] in the K-major core-
-    // matrix layout, TF32 hi part then lo part, each TN x TK floats
+    // tcgen05 volume operator (shapes v = 3, 4): A operand D^T[a][(l, c)] (rows a padded to 64)
+    // in the K-major core-matrix layout, TF32 hi part then lo part, each 64 x TK floats
     const float* Dtc;
     void* state;                // [rhs][ne][nf][nb]
     int64_t rhs_stride;         // ne * nf * nb
@@ -136,14 +136,14 @@ struct Shape {
     static constexpr int BW1 = dim_pk(DIM, DC1 + 1);
     static constexpr int DC2 = degree_of(DIM, NWG);
     static constexpr int BW2 = dim_pk(DIM, DC2 - 2);
-    // tcgen05 volume operator: K = (direction l, row c < NBM) padded to the MMA's k = 8, N = basis
-    // functions a padded to 16, the accumulators of two 128-row chunks in TCOLS TMEM columns; the
-    // volume result goes to shared memory with the odd row stride VS (conflict-free banks)
+    // tcgen05 volume operator: M = 64 rows a (basis functions, NB used), N = the patch's
+    // (element, field) rows padded to 16 (at most TCOLS = 256 TMEM columns), K = (direction l,
+    // row c < NBM) padded to the MMA's k = 8; the volume result goes to shared memory with the
+    // odd row stride VS (conflict-free banks)
     static constexpr int TK = (DIM * NBM + 7) / 8 * 8;
-    static constexpr int TN = (NB + 15) / 16 * 16;
-    static constexpr int TCOLS = 2 * TN <= 32 ? 32 : 2 * TN <= 64 ? 64 : 2 * TN <= 128 ? 128 : 256;
+    static constexpr int TCOLS = 256;
     static constexpr int VS = NB % 2 ? NB : NB + 1;
-    static_assert(!TC5 || (DIM == 3 && VS <= TK && 2 * TN <= TCOLS), "tcgen05 volume layout");
+    static_assert(!TC5 || (DIM == 3 && NB <= 64 && VS <= 2 * TK), "tcgen05 volume layout");
 };
 
 // CTAs per SM the register budget is shaped for (two 256-thread CTAs fit the FP32 3D
@@ -205,8 +205,8 @@ struct SmemLayout {
     static __host__ __device__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
     size_t off_Y, off_Ylo, off_Ua, off_Ub, off_W, off_tr, off_Gi, off_gphi, off_gdel, off_mat, off_ac, off_gd,
         off_nrm, off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, off_pair, off_own, bytes, state_bytes, tr_bytes;
-    size_t off_tA, off_tB, off_tbar;   // tcgen05 operands (hi, lo parts), mbarriers + TMEM address
-    int tc_rows;                       // A-operand rows: 128-row chunks cover (element, field) rows
+    size_t off_tW, off_tD, off_tbar;   // tcgen05 operands (hi, lo parts), mbarriers + TMEM address
+    int tc_rows;                       // rows of the W operand: (element, field) rows padded to 16
     bool split, factored, twobuf, rk4;   // rk4: Y at the sub-step start (Ylo slot), stage input (Ub)
     // mode (see ModeTraits): split carries the Taylor accumulator Y as an unevaluated pair
     // hi + lo (one more patch-state buffer); the SIMT modes use the factored volume term (a W
@@ -240,12 +240,11 @@ struct SmemLayout {
         off_pair = o; o = align16(o + (size_t)mp * 2 + 4);
         off_own = o; o = align16(o + (size_t)mp * DIM * 2 + 4);
         tc_rows = 0;
-        off_tA = off_tB = off_tbar = o;
+        off_tW = off_tD = off_tbar = o;
         if (Sh::TC5) {
-            const int r = (mp * Sh::NF + 7) / 8 * 8;
-            tc_rows = r < 128 ? 128 : r;
-            off_tA = o = (o + 127) & ~size_t(127); o += (size_t)2 * tc_rows * Sh::TK * sizeof(float);
-            off_tB = o; o += (size_t)2 * Sh::TN * Sh::TK * sizeof(float);
+            tc_rows = (mp * Sh::NF + 15) / 16 * 16;
+            off_tW = o = (o + 127) & ~size_t(127); o += (size_t)2 * tc_rows * Sh::TK * sizeof(float);
+            off_tD = o; o += (size_t)2 * 64 * Sh::TK * sizeof(float);
             off_tbar = o; o += 32;
         }
         bytes = o;
@@ -299,10 +298,10 @@ struct TentCtx {
     int8_t* sOwn;                         // [facet][2]: (slot, facet position) owning each facet
     int* sNpair;
     int* sNown;
-    // tcgen05 volume operator: A operand hi / lo, B operand (D tables) hi / lo, volume result
-    // (over the A hi part once the MMAs have read it), mbarriers [MMA done, tables loaded] and
-    // [TMEM address, MMA phase, failure flag]
-    float *sAh, *sAl, *sBh, *sBl, *sVol;
+    // tcgen05 volume operator: W operand (the MMA's B) hi / lo, D table (the MMA's A) hi / lo,
+    // volume result (over the W operand once the MMAs have read it), mbarriers [MMA done, table
+    // loaded] and [TMEM address, MMA phase, failure flag]
+    float *sWh, *sWl, *sDh, *sDl, *sVol;
     uint64_t* sBar;
     uint32_t* sTc;
     int tc_rows;
@@ -337,15 +336,15 @@ struct TentCtx {
         sNown = (int*)(smem + lay.off_own);
         tc_rows = lay.tc_rows;
         if (Sh::TC5) {
-            sAh = (float*)(smem + lay.off_tA);
-            sAl = sAh + (size_t)lay.tc_rows * Sh::TK;
-            sBh = (float*)(smem + lay.off_tB);
-            sBl = sBh + Sh::TN * Sh::TK;
-            sVol = sAh;
+            sWh = (float*)(smem + lay.off_tW);
+            sWl = sWh + (size_t)lay.tc_rows * Sh::TK;
+            sDh = (float*)(smem + lay.off_tD);
+            sDl = sDh + 64 * Sh::TK;
+            sVol = sWh;
             sBar = (uint64_t*)(smem + lay.off_tbar);
             sTc = (uint32_t*)(smem + lay.off_tbar + 16);
         } else {
-            sAh = sAl = sBh = sBl = sVol = nullptr;
+            sWh = sWl = sDh = sDl = sVol = nullptr;
             sBar = nullptr;
             sTc = nullptr;
         }
@@ -356,7 +355,7 @@ struct TentCtx {
 // tcgen05 primitives (inline PTX, sm_103a) for the volume operator of kernel shapes v = 3, 4.
 // Operands live in shared memory in the no-swizzle K-major layout: 8-row x 16-byte core
 // matrices, the 4-element k groups of one 8-row group 128 B apart, 8-row groups TK x 32 B
-// apart; the accumulator of a 128-row MMA occupies TMEM lanes 0..127 (one row per lane).
+// apart; the FP32 accumulator of a 64-row MMA keeps row r in TMEM lane 32 (r / 16) + r % 16.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ uint32_t tf32_bits(float x) {
@@ -407,13 +406,13 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t v[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Once per CTA before its first tent: zero the A operand (its K padding and spare rows must be
-// finite), initialise the two mbarriers, bring both parts of the D tables into shared memory with
+// Once per CTA before its first tent: zero the W operand (its K padding and spare rows must be
+// finite), initialise the two mbarriers, bring both parts of the D table into shared memory with
 // one bulk asynchronous copy (the TMA engine's non-tensor form) and allocate the TMEM columns.
 template <typename Real, int DIM, int P>
 __device__ void tc5_begin(TentCtx<Real, DIM, P>& c, const KArgs& a) {
     using Sh = Shape<DIM, P>;
-    float4* A4 = (float4*)c.sAh;
+    float4* A4 = (float4*)c.sWh;
     const int n4 = 2 * c.tc_rows * Sh::TK / 4;
     for (int i = threadIdx.x; i < n4; i += Sh::NT) A4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     if (threadIdx.x == 0) {
@@ -426,10 +425,10 @@ __device__ void tc5_begin(TentCtx<Real, DIM, P>& c, const KArgs& a) {
     __syncthreads();
     const bool have_tables = a.Dtc != nullptr;
     if (threadIdx.x == 0 && have_tables) {
-        const uint32_t bytes = 2u * Sh::TN * Sh::TK * 4u, bar = smem_u32(&c.sBar[1]);
+        const uint32_t bytes = 2u * 64u * Sh::TK * 4u, bar = smem_u32(&c.sBar[1]);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                         smem_u32(c.sBh)),
+                         smem_u32(c.sDh)),
                      "l"(a.Dtc), "r"(bytes), "r"(bar)
                      : "memory");
     }
@@ -462,35 +461,29 @@ __device__ void tc5_end(TentCtx<Real, DIM, P>& c) {
                      : "memory");
 }
 
-// One thread issues the stage's volume MMAs: for each 128-row chunk of (element, field) rows
-// (the second chunk ends at the last row), D[rows][a] = sum over k of A[rows][k] B[a][k] as
-// A_lo B_hi + A_hi B_lo + A_hi B_hi, TF32 operands, FP32 accumulation in TMEM, then a commit
-// to the MMA mbarrier.
+// One thread issues the stage's volume MMAs: vol[a][(k, f)] = sum over K of D[a][K] W[(k, f)][K]
+// as D_lo W_hi + D_hi W_lo + D_hi W_hi (TF32 operands, FP32 accumulation in TMEM; M = 64 rows a,
+// N = the tent's (element, field) rows padded to 16), then a commit to the MMA mbarrier.
 template <typename Real, int DIM, int P>
 __device__ void tc5_issue(TentCtx<Real, DIM, P>& c) {
     using Sh = Shape<DIM, P>;
     constexpr uint32_t SBO = Sh::TK * 32;
-    constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(Sh::TN >> 3) << 17) |
-                               ((uint32_t)(128 >> 4) << 24);
+    const uint32_t n = (uint32_t)((c.ns * Sh::NF + 15) / 16 * 16);
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((n >> 3) << 17) | ((uint32_t)(64 >> 4) << 24);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tbase = c.sTc[0];
-    const int nch = c.ns * Sh::NF > 128 ? 2 : 1;
-    const uint32_t aop[2] = {smem_u32(c.sAh), smem_u32(c.sAl)}, bop[2] = {smem_u32(c.sBh), smem_u32(c.sBl)};
-    for (int ch = 0; ch < nch; ++ch) {
-        const uint32_t r0 = ch == 0 ? 0u : (uint32_t)(c.tc_rows - 128);
-        const uint32_t d = tbase + (uint32_t)(ch * Sh::TN);
-        uint32_t acc = 0;
-        for (int t = 0; t < 3; ++t) {
-            const uint32_t A = aop[t == 0 ? 1 : 0] + (r0 / 8) * SBO, B = bop[t == 1 ? 1 : 0];
-            for (int s = 0; s < Sh::TK / 8; ++s) {
-                const uint64_t ad = tc_desc(A + s * 256, 128, SBO), bd = tc_desc(B + s * 256, 128, SBO);
-                asm volatile(
-                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                    "l"(ad), "l"(bd), "r"(IDESC), "r"(acc)
-                    : "memory");
-                acc = 1;
-            }
+    const uint32_t d = c.sTc[0];
+    const uint32_t dop[2] = {smem_u32(c.sDh), smem_u32(c.sDl)}, wop[2] = {smem_u32(c.sWh), smem_u32(c.sWl)};
+    uint32_t acc = 0;
+    for (int t = 0; t < 3; ++t) {
+        const uint32_t A = dop[t == 0 ? 1 : 0], B = wop[t == 1 ? 1 : 0];
+        for (int s = 0; s < Sh::TK / 8; ++s) {
+            const uint64_t ad = tc_desc(A + s * 256, 128, SBO), bd = tc_desc(B + s * 256, 128, SBO);
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+            acc = 1;
         }
     }
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -498,13 +491,14 @@ __device__ void tc5_issue(TentCtx<Real, DIM, P>& c) {
                  : "memory");
 }
 
-// All threads: wait (bounded) for the stage's MMAs, then the warps copy the accumulators of
-// their TMEM lane quarter to sVol[(element, field) row][a] (row stride VS) over the A operand,
-// which the finished MMAs no longer read.
+// All threads: wait (bounded) for the stage's MMAs, then the warps of the lane quarters that
+// hold basis functions copy the accumulators to sVol[(k, f)][a] (row stride VS) over the W
+// operand, which the finished MMAs no longer read.  A 64-row accumulator keeps row a in TMEM
+// lane 32 (a / 16) + a % 16, column (k, f): lanes 0..15 of each quarter.
 template <typename Real, int DIM, int P>
 __device__ void tc5_collect(TentCtx<Real, DIM, P>& c, const KArgs& a, uint32_t parity) {
     using Sh = Shape<DIM, P>;
-    constexpr int NCB = Sh::TN / 16, VS = Sh::VS, NB = Sh::NB;
+    constexpr int VS = Sh::VS, NB = Sh::NB, NQ = (NB + 15) / 16;
     if (c.sTc[2] == 0 && !tc_wait(&c.sBar[0], parity)) {
         atomicCAS(a.err, 0, 3);
         c.sTc[2] = 1;
@@ -512,20 +506,19 @@ __device__ void tc5_collect(TentCtx<Real, DIM, P>& c, const KArgs& a, uint32_t p
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, q = warp & 3;
     const int rows = c.ns * Sh::NF;
-    const int nch = rows > 128 ? 2 : 1;
+    const int ncb = (rows + 15) / 16;
     const uint32_t tbase = c.sTc[0];
-    for (int u = warp >> 2; u < nch * NCB; u += Sh::NT / 128) {
-        const int ch = u / NCB, cb = u - ch * NCB;
-        const int r0 = (ch == 0 ? 0 : c.tc_rows - 128) + 32 * q;   // row of this quarter's lane 0
-        if (r0 >= rows || (ch == 1 && r0 + 31 < 128)) continue;     // warp-uniform
-        uint32_t v[16];
-        tc_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(ch * Sh::TN + cb * 16), v);
-        const int r = r0 + lane;
-        if (r < rows && (ch == 0 || r >= 128)) {
+    if (q < NQ) {
+        const int av = lane < 16 ? 16 * q + lane : NB;
+        for (int cb = warp >> 2; cb < ncb; cb += Sh::NT / 128) {
+            uint32_t v[16];
+            tc_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(cb * 16), v);
+            if (av < NB) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = cb * 16 + j;
-                if (col < NB) c.sVol[r * VS + col] = __uint_as_float(v[j]);
+                for (int j = 0; j < 16; ++j) {
+                    const int r = cb * 16 + j;
+                    if (r < rows) c.sVol[r * VS + av] = __uint_as_float(v[j]);
+                }
             }
         }
     }
@@ -814,9 +807,9 @@ __device__ __forceinline__ void tent_w_item(TentCtx<Real, DIM, P>& c, const KArg
 #pragma unroll 1
     for (int b = B1c; b < NBP; b += W) block(b, I1{}, I2{});
     if constexpr (Sh::TC5 && DIM == 3) {
-        // A operand of the tcgen05 volume term: the curl combination folded into W,
-        // A[(k, f)][(l, c)] = (E rows: -a_l x W_H, H rows: a_l x W_E)_f, so that the MMA with
-        // B[a][(l, c)] = D_l^T[a][c] gives the element's volume term directly; TF32 hi + lo
+        // W operand of the tcgen05 volume term: the curl combination folded into W,
+        // Wt[(k, f)][(l, c)] = (E rows: -a_l x W_H, H rows: a_l x W_E)_f, so that the MMA with
+        // D[a][(l, c)] = D_l^T[a][c] gives the element's volume term directly; TF32 hi + lo
         const Real* ac = c.sAc + k0 * DIM * 3;
 #pragma unroll
         for (int ci = 0; ci < AP; ++ci) {
@@ -832,8 +825,8 @@ __device__ __forceinline__ void tent_w_item(TentCtx<Real, DIM, P>& c, const KArg
                     for (int f = 0; f < 6; ++f) {
                         const int o = tc_off<Sh::TK>(k0 * 6 + f, l * NBM + row);
                         const float h = __uint_as_float(tf32_bits(v[f]));
-                        c.sAh[o] = h;
-                        c.sAl[o] = __uint_as_float(tf32_bits(v[f] - h));
+                        c.sWh[o] = h;
+                        c.sWl[o] = v[f] - h;   // exact; the MMA reads its top 19 bits
                     }
                 }
             }
@@ -861,7 +854,8 @@ __device__ __forceinline__ void tent_w_item(TentCtx<Real, DIM, P>& c, const KArg
 // last round of trace items leaves idle
 template <typename Real, int DIM, int P>
 __device__ void tent_traces(TentCtx<Real, DIM, P>& c, const KArgs& a, const Real* Ucur, Real* tr) {
-    if (c.sW || Shape<DIM, P>::TC5) {   // W = M_j U, or the tcgen05 A operand built from it
+    // W = M_j U (or the tcgen05 W operand built from it) on the threads the trace items leave idle
+    if (c.sW || Shape<DIM, P>::TC5) {
         constexpr int NT = Shape<DIM, P>::NT;
         const int nitems = ((sizeof(Real) == 4 && Shape<DIM, P>::PAIRS) ? *c.sNpair : c.ns) * Shape<DIM, P>::NWG;
         const int busy = (c.ns * Shape<DIM, P>::NCG) % NT, idle = NT - busy;
@@ -1253,7 +1247,7 @@ __device__ void tent_sat(TentCtx<Real, DIM, P>& c, const KArgs& a, Real* tape) {
     constexpr int ESZ = Shape<DIM, P>::NF * Shape<DIM, P>::NBP;
     const size_t slot = (size_t)a.max_patch * ESZ;
     if constexpr (Shape<DIM, P>::TC5) {
-        // SIMT traces (+ A operand), fluxes and epilogue; the volume MMAs run on the tensor
+        // SIMT traces (+ W operand), fluxes and epilogue; the volume MMAs run on the tensor
         // cores while the fluxes are computed.  U is updated in place.
         Real* U = c.sUa;
         uint32_t ph = c.sTc[1];
@@ -1264,7 +1258,7 @@ __device__ void tent_sat(TentCtx<Real, DIM, P>& c, const KArgs& a, Real* tape) {
             __syncthreads();
             for (int n = 1; n <= a.q; ++n) {
                 tent_traces(c, a, U, c.sTr);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // A visible to the MMAs
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // W operand visible to the MMAs
                 __syncthreads();
                 if (threadIdx.x == 0) tc5_issue(c);
                 tent_fluxes(c, c.sTr);
