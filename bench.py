@@ -42,8 +42,8 @@ KERNEL_SOURCES = ["paper_1906_11029_gb300/csrc/mtp_kernels.cuh", "paper_1906_110
 # reports traffic null.
 TRAFFIC_BYTES_PER_TENT = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum on the launch that applies layers
-    # 1000..1099 (81 105 tents) of the graded 32^3 p = 4 workload: 1.134 GB + 0.745 GB
-    ("fp32", "tent_persistent_kernel"): {"bytes_per_tent": 23160.5, "sources": "7aa5735501a53fdc"},
+    # 1000..1099 (81 105 tents) of the graded 32^3 p = 4 workload: 1.145 GB + 0.757 GB
+    ("fp32", "tent_persistent_kernel"): {"bytes_per_tent": 23455.2, "sources": "215962c12a1e8c1c"},
 }
 
 
@@ -519,6 +519,8 @@ def run_mtp(args):
     tents = mesh.pitch(w.T, w.causality)
     if args.variant:
         tents.set_variant(args.variant)
+    if args.launch:
+        tents.set_launch(args.launch)
     t2 = time.perf_counter()
     tents_dev = mesh.pitch(w.T, w.causality, device=True)    # same tent list, rounds on the GPU
     t3 = time.perf_counter()
@@ -575,11 +577,13 @@ def run_mtp(args):
         peak, src = probe["fp64_fma"], "mtp_probe_rates FP64 FMA loop on this device, this run"
     achieved = flops_per_launch / (launch_ms / 1e3) / 1e12
     kname = "tent_persistent_kernel" if persistent else "tent_layer_kernel"
-    tpl = traffic_per_tent(args.precision, kname) if args.workload == "graded" else None
+    # the stored traffic is the default kernel's (variant 0, occupancy-limit DAG walk)
+    default_kernel = args.variant == 0 and args.launch == 0
+    tpl = traffic_per_tent(args.precision, kname) if args.workload == "graded" and default_kernel else None
     traffic = None if tpl is None else tpl * tents.info["n_tents"] / launches_per_step
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": f"{kname}<{args.precision},3,{w.p}>", "kernel_variant": args.variant, "peak_source": src,
+                "kernel": f"{kname}<{args.precision},3,{w.p}>", "kernel_variant": args.variant, "launch": args.launch, "peak_source": src,
                 "probe_tflops": probe, "fp32_unit_count_peak": unit_peak, "sms": n_sms,
                 "frac_of_unit_count_peak": achieved / unit_peak if prec == mtp.MTP_FP32 else None,
                 "kernel_sources": kernel_source_hash()}
@@ -678,6 +682,8 @@ def main():
     ap.add_argument("--fp64-window", type=float, default=0.02)
     ap.add_argument("--layer-launches", action="store_true", help="one launch per layer instead of the DAG walk")
     ap.add_argument("--variant", type=int, default=0, help="tent kernel shape variant (mtp_tents_set_variant)")
+    ap.add_argument("--launch", type=int, default=0, choices=[0, 1],
+                    help="DAG walk at the occupancy limit (0) or with one CTA per SM (1) (mtp_tents_set_launch)")
     ap.add_argument("--cpu-tents", type=int, default=80, help="oracle baseline: tents (per process)")
     ap.add_argument("--cpu-rounds", type=int, default=80)
     ap.add_argument("--ref-tents", type=int, default=20, help="reference arm: tents per host core per step")

@@ -515,6 +515,7 @@ static void fill_args(Tents& t, void* state, KArgs& a) {
     a.m = m.m;
     a.max_patch = m.max_patch;
     double f = 1.0;
+    for (int i = 0; i <= kMaxSub; ++i) a.tsub[i] = i <= m.m ? (double)i / (double)m.m : 1.0;
     for (int n = 0; n < kMaxTaylor; ++n) {
         if (n > 0) f = f / (double)m.m / (double)n;
         a.taylor[n] = f;

@@ -34,6 +34,7 @@
 namespace mtp {
 
 constexpr int kMaxTaylor = 9;
+constexpr int kMaxSub = 64;   // largest number m of SAT sub-intervals the options accept
 
 struct KArgs {
     const int32_t* tent_v;
@@ -73,6 +74,7 @@ struct KArgs {
     int q, m;
     int max_patch;
     double taylor[kMaxTaylor];  // (1/m)^n / n!
+    double tsub[kMaxSub + 1];   // sub-interval starts i / m, i = 0..m
 };
 
 __host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
@@ -203,7 +205,7 @@ template <typename Real, int DIM, int P>
 struct SmemLayout {
     using Sh = Shape<DIM, P>;
     static __host__ __device__ size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-    size_t off_Y, off_Ylo, off_Ua, off_Ub, off_W, off_tr, off_Gi, off_gphi, off_gdel, off_mat, off_ac, off_gd,
+    size_t off_Y, off_Ylo, off_Ua, off_Ub, off_W, off_tr, off_Gi, off_gphi, off_gdel, off_mat, off_ac, off_gd, off_gpr,
         off_nrm, off_liftc, off_trs, off_Z, off_j, off_nslot, off_nfi, off_pair, off_own, bytes, state_bytes, tr_bytes;
     size_t off_tW, off_tD, off_tbar;   // tcgen05 operands (hi, lo parts), mbarriers + TMEM address
     int tc_rows;                       // rows of the W operand: (element, field) rows padded to 16
@@ -230,6 +232,7 @@ struct SmemLayout {
         off_mat = o; o = align16(o + (size_t)mp * 2 * sizeof(double));
         off_ac = o; o = align16(o + (size_t)mp * DIM * 3 * sizeof(Real));
         off_gd = o; o = align16(o + (size_t)mp * 3 * sizeof(Real));
+        off_gpr = o; o = align16(o + (size_t)mp * 5 * sizeof(Real));
         off_nrm = o; o = align16(o + (size_t)mp * DIM * 3 * sizeof(Real));
         off_liftc = o; o = align16(o + (size_t)mp * DIM * sizeof(Real));
         off_trs = o; o = align16(o + (size_t)mp * sizeof(Real));
@@ -294,6 +297,7 @@ struct TentCtx {
     Real* sY0;                                     // RK4 mode: Y at the start of the sub-step
     double *sGphi, *sGdel, *sMat;
     Real *sAc, *sGd, *sNrm, *sLiftc, *sTrs, *sZ;
+    Real* sGpr;   // [k][5]: grad phi at the tent bottom, eps, mu in the state precision
     int8_t *sJ, *sNslot, *sNfi, *sPair;   // sPair: [pair][2] element slots (second -1: single)
     int8_t* sOwn;                         // [facet][2]: (slot, facet position) owning each facet
     int* sNpair;
@@ -323,6 +327,7 @@ struct TentCtx {
         sMat = (double*)(smem + lay.off_mat);
         sAc = (Real*)(smem + lay.off_ac);
         sGd = (Real*)(smem + lay.off_gd);
+        sGpr = (Real*)(smem + lay.off_gpr);
         sNrm = (Real*)(smem + lay.off_nrm);
         sLiftc = (Real*)(smem + lay.off_liftc);
         sTrs = (Real*)(smem + lay.off_trs);
@@ -563,6 +568,9 @@ __device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t ten
             for (int q = 0; q < 3; ++q) c.sAc[(k * DIM + l) * 3 + q] = (Real)(dt * g[3 * (l + 1) + q]);
         c.sMat[2 * k] = g[29];
         c.sMat[2 * k + 1] = g[30];
+        for (int q = 0; q < 3; ++q) c.sGpr[5 * k + q] = (Real)gp[q];
+        c.sGpr[5 * k + 3] = (Real)g[29];
+        c.sGpr[5 * k + 4] = (Real)g[30];
         c.sZ[k * (1 + DIM)] = (Real)g[31];
         c.sTrs[k] = (Real)g[28];
         c.sJ[k] = (int8_t)j;
@@ -641,36 +649,31 @@ __device__ void tent_setup(TentCtx<Real, DIM, P>& c, const KArgs& a, int64_t ten
 // one row per thread, in the state precision.  The causality test |g| < sqrt(eps mu) at
 // t_i (and at the tent top when i = 0) decides an error and is taken in FP64.
 template <typename Real, int DIM, int P>
-__device__ void tent_ginv_into(TentCtx<Real, DIM, P>& c, const KArgs& a, double ti, bool check_top, Real* dst,
+__device__ void tent_ginv_into(TentCtx<Real, DIM, P>& c, const KArgs& a, double ti, Real tr, bool check, Real* dst,
                                int t0, int nthr) {
     using Sh = Shape<DIM, P>;
     constexpr int NF = Sh::NF;
     const int me = (int)threadIdx.x - t0;
     if (me < 0) return;
-    for (int k = me; k < c.ns; k += nthr) {
-        const double eps = c.sMat[2 * k], mu = c.sMat[2 * k + 1];
-        double gg = 0;
-        for (int q = 0; q < 3; ++q) {
-            const double g = c.sGphi[3 * k + q] + ti * c.sGdel[3 * k + q];
-            gg += g * g;
-        }
-        if (!(gg < eps * mu)) atomicCAS(a.err, 0, 1);
-        if (check_top) {   // grad phi is affine in t, so bottom and top bound the whole tent
-            double gt = 0;
+    if (check)   // grad phi is affine in t^, so |grad phi|^2 is convex: bottom and top bound the tent
+        for (int k = me; k < c.ns; k += nthr) {
+            const double eps = c.sMat[2 * k], mu = c.sMat[2 * k + 1];
+            double gg = 0, gt = 0;
             for (int q = 0; q < 3; ++q) {
-                const double g = c.sGphi[3 * k + q] + c.sGdel[3 * k + q];
-                gt += g * g;
+                const double g = c.sGphi[3 * k + q] + ti * c.sGdel[3 * k + q];
+                const double h = c.sGphi[3 * k + q] + c.sGdel[3 * k + q];
+                gg += g * g;
+                gt += h * h;
             }
-            if (!(gt < eps * mu)) atomicCAS(a.err, 0, 1);
+            if (!(gg < eps * mu) || !(gt < eps * mu)) atomicCAS(a.err, 0, 1);
         }
-    }
-    const Real tr = (Real)ti;
     for (int idx = me; idx < c.ns * NF; idx += nthr) {
         const int k = idx / NF, R = field6<DIM>(idx - k * NF);
+        const Real* gp = c.sGpr + 5 * k;
         Real g[3];
 #pragma unroll
-        for (int q = 0; q < 3; ++q) g[q] = (Real)c.sGphi[3 * k + q] + tr * (Real)c.sGdel[3 * k + q];
-        const Real eps = (Real)c.sMat[2 * k], mu = (Real)c.sMat[2 * k + 1], em = eps * mu;
+        for (int q = 0; q < 3; ++q) g[q] = gp[q] + tr * c.sGd[3 * k + q];
+        const Real eps = gp[3], mu = gp[4], em = eps * mu;
         const Real s = Real(1) / (em - (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]));
         const int rq = R < 3 ? R : R - 3;                  // component of the row's field
         const Real d = s * (R < 3 ? mu : eps);             // diagonal block: s mu P or s eps P
@@ -692,13 +695,13 @@ __device__ void tent_ginv_into(TentCtx<Real, DIM, P>& c, const KArgs& a, double 
 
 template <typename Real, int DIM, int P>
 __device__ __forceinline__ void tent_ginv_at(TentCtx<Real, DIM, P>& c, const KArgs& a, double ti, bool check_top) {
-    tent_ginv_into(c, a, ti, check_top, c.sGi, 0, (int)blockDim.x);
+    tent_ginv_into(c, a, ti, (Real)ti, check_top, c.sGi, 0, (int)blockDim.x);
 }
 
 // G(t_i)^-1 at the start of sub-interval i (the tent bottom and top are checked at i = 0)
 template <typename Real, int DIM, int P>
 __device__ __forceinline__ void tent_ginv(TentCtx<Real, DIM, P>& c, const KArgs& a, int i) {
-    tent_ginv_at(c, a, (double)i / (double)a.m, i == 0);
+    tent_ginv_into(c, a, 0.0, (Real)a.tsub[i], i == 0, c.sGi, 0, (int)blockDim.x);
 }
 
 // Error-free sum of two floats (Knuth's two-sum): hi + lo == a + b exactly, hi = fl(a + b).
