@@ -356,19 +356,25 @@ def lattice_interpolation(dim, p_from, p_to):
 def run_equal_error(args):
     """Discretisation error of the p = 4 graded workload estimated against p = 5 on the same mesh
     and tents (u4 interpolated exactly to the p = 5 lattice), next to the distance of each
-    FP32-state mode from the FP32 SIMT path and from each other."""
+    FP32-state mode (and of kernel variant 3, the volume term on tcgen05) from the FP32 SIMT path
+    and from each other."""
     import torch
     import mtp_synth as S
     import paper_1906_11029_gb300 as mtp
     w4 = make_workload(args.workload)
     out, times, dofs = {}, {}, {}
+    TC5 = "tc5"   # MTP_FP32 with kernel variant 3
     runs = [(5, mtp.MTP_FP32), (4, mtp.MTP_FP32), (4, mtp.MTP_TF32), (4, mtp.MTP_TF32X3), (4, mtp.MTP_FP32_SPLIT)]
+    if w4.dim == 3 and w4.p == 4:
+        runs.append((4, TC5))
     if args.equal_error_fp64:
         runs.append((4, mtp.MTP_FP64))
     for p, prec in runs:
         w = S.graded_sphere(32, p, 0.5) if args.workload == "graded" else w4
-        mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=p, precision=prec)
+        mesh = mtp.Mesh(w.dim, w.verts, w.elems, w.eps, w.mu, p=p, precision=mtp.MTP_FP32 if prec == TC5 else prec)
         tents = mesh.pitch(w.T, w.causality)
+        if prec == TC5:
+            tents.set_variant(3)
         st = mesh.state_from_lattice(torch.tensor(initial_lattice(w)[None], device="cuda"))
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
@@ -385,16 +391,19 @@ def run_equal_error(args):
     ref = out[(4, mtp.MTP_FP32)]
     rel = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))
     names = {mtp.MTP_FP32: "fp32", mtp.MTP_TF32: "tf32", mtp.MTP_TF32X3: "tf32x3", mtp.MTP_FP64: "fp64",
-             mtp.MTP_FP32_SPLIT: "fp32split"}
+             mtp.MTP_FP32_SPLIT: "fp32split", TC5: "tcgen05_variant3"}
     res = {"workload": w4.name, "e_disc_p4_vs_p5": rel(up(ref), u5),
            "ms": {f"p{p}_{names[q]}": v for (p, q), v in times.items()}}
-    for q in (mtp.MTP_TF32, mtp.MTP_TF32X3, mtp.MTP_FP32_SPLIT):
-        res[f"{names[q]}_vs_fp32"] = rel(out[(4, q)], ref)
+    for q in (mtp.MTP_TF32, mtp.MTP_TF32X3, mtp.MTP_FP32_SPLIT, TC5):
+        if (4, q) in out:
+            res[f"{names[q]}_vs_fp32"] = rel(out[(4, q)], ref)
     if (4, mtp.MTP_FP64) in out:
         # the whole evolve to T in FP64: each FP32-state mode against it, and against e_disc
         u64 = out[(4, mtp.MTP_FP64)]
         res["e_disc_fp64_p4_vs_p5"] = rel(up(u64), u5)
-        for q in (mtp.MTP_FP32, mtp.MTP_TF32, mtp.MTP_TF32X3, mtp.MTP_FP32_SPLIT):
+        for q in (mtp.MTP_FP32, mtp.MTP_TF32, mtp.MTP_TF32X3, mtp.MTP_FP32_SPLIT, TC5):
+            if (4, q) not in out:
+                continue
             d = rel(out[(4, q)], u64)
             res[f"{names[q]}_vs_fp64_full_T"] = d
             res[f"{names[q]}_vs_fp64_over_e_disc"] = d / res["e_disc_fp64_p4_vs_p5"]

@@ -71,6 +71,27 @@ def test_tcgen05_variants_match_oracle_and_variant0(name):
             assert rel_l2(v1, v0) <= 5e-6
 
 
+def test_tcgen05_variant_multi_rhs_equals_single():
+    """Several right-hand sides in one DAG-walk CTA (the MMA mbarrier phase carries over from
+    one right-hand side and tent to the next) and in per-layer launches (one CTA per tent and
+    right-hand side): each equals its own single-RHS evolve."""
+    w = S.cube_mode(2, 3, 0.1)
+    rng = np.random.default_rng(17)
+    m1 = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=3, precision=mtp.MTP_FP32)
+    stack = rng.standard_normal((3,) + tuple(m1.lattice_shape[1:]))
+    singles = [_run(w, stack[r], 3) for r in range(3)]
+    for launch in (0, 2):
+        m = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=3, precision=mtp.MTP_FP32, n_rhs=3)
+        t = m.pitch(w.T, w.causality)
+        t.set_variant(3)
+        t.set_launch(launch)
+        st = m.state_from_lattice(torch.tensor(stack, device=DEV))
+        t.evolve(st)
+        many = m.state_to_lattice(st).cpu().numpy()
+        for r in range(3):
+            assert np.array_equal(many[r], singles[r]), (launch, r, rel_l2(many[r], singles[r]))
+
+
 def test_variants_refused_outside_fp32():
     w = S.cube_mode(2, 2, 0.1)
     m = mtp.Mesh(3, w.verts, w.elems, w.eps, w.mu, p=2, precision=mtp.MTP_FP64)
