@@ -73,3 +73,15 @@ def test_algorithmic_flops_per_dof_update(dim, p, flop):
     facets d n_f 2 N_fp N_p and mass solve + M' 2 n_f^2 N_p multiply-adds, 2 flop each,
     divided by the n_f N_p DOFs updated."""
     assert _bench().flops_per_dof_update(dim, p) == pytest.approx(flop)
+
+
+def test_traffic_figure_is_tied_to_the_kernel_sources(monkeypatch):
+    """The stored DRAM traffic per tent is reported only while the kernel sources hash to the
+    stamp taken with it; any change to the sources turns it into null."""
+    bench = _bench()
+    rec = bench.TRAFFIC_BYTES_PER_TENT[("fp32", "tent_persistent_kernel")]
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: rec["sources"])
+    assert bench.traffic_per_tent("fp32", "tent_persistent_kernel") == rec["bytes_per_tent"]
+    assert bench.traffic_per_tent("fp64", "tent_persistent_kernel") is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 16)
+    assert bench.traffic_per_tent("fp32", "tent_persistent_kernel") is None
